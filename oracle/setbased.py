@@ -1,0 +1,94 @@
+"""Second, independent restatement of the round-synchronous coloring, in sets.
+
+TEST INFRASTRUCTURE.  Written separately from ``pgc_oracle.c`` (no shared
+code) so that the two can be cross-checked on many tiny graphs.  Pure Python,
+for graphs of a few dozen vertices.
+
+The neighborhood S(v) is materialised as a Python set, priorities as tuples
+compared lexicographically: key(v) = (deg(v), -rand(v), -v), with the
+degree term dropped when the recolorDegrees rule is off.  "u beats v" means
+key(u) > key(v); that is Alg. 4 (Sec. 3.3) written as one comparison.
+"""
+from __future__ import annotations
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """splitmix64 output for state x (Steele, Lea, Flood 2014)."""
+    z = (x + 0x9E3779B97F4A7C15) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def adjacency_sets(row_ptr, col_idx):
+    n = len(row_ptr) - 1
+    return [set(int(u) for u in col_idx[row_ptr[v]:row_ptr[v + 1]]) - {v} for v in range(n)]
+
+
+def neighborhoods(kind, row_ptr, col_idx, col_ptr=None, row_idx=None):
+    """S(v) for D1 ('d1'), D2 ('d2') or PD2 ('pd2', columns)."""
+    if kind == "pd2":
+        n_cols = len(col_ptr) - 1
+        rows = [set(int(c) for c in col_idx[row_ptr[r]:row_ptr[r + 1]])
+                for r in range(len(row_ptr) - 1)]
+        out = []
+        for v in range(n_cols):
+            s = set()
+            for r in col_idx_rows(col_ptr, row_idx, v):
+                s |= rows[r]
+            s.discard(v)
+            out.append(s)
+        return out
+    adj = adjacency_sets(row_ptr, col_idx)
+    if kind == "d1":
+        return adj
+    out = []
+    for v, nb in enumerate(adj):
+        s = set(nb)
+        for u in nb:
+            s |= adj[u]
+        s.discard(v)
+        out.append(s)
+    return out
+
+
+def col_idx_rows(col_ptr, row_idx, v):
+    return [int(r) for r in row_idx[col_ptr[v]:col_ptr[v + 1]]]
+
+
+def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, row_idx=None):
+    """Returns (colors, rounds, num_colors, worklist sizes per round)."""
+    S = neighborhoods(kind, row_ptr, col_idx, col_ptr, row_idx)
+    n = len(S)
+    if kind == "pd2":
+        deg = [col_ptr[v + 1] - col_ptr[v] for v in range(n)]
+    else:
+        deg = [row_ptr[v + 1] - row_ptr[v] for v in range(n)]
+
+    def key(v):
+        h = splitmix64((seed ^ v) & MASK64)
+        return (deg[v], -h, -v) if recolor_degrees else (-h, -v)
+
+    final = {}
+    todo = set(range(n))
+    sizes = []
+    while todo:
+        sizes.append(len(todo))
+        tentative = {}
+        for v in todo:
+            used = {final[u] for u in S[v] if u in final}
+            c = 1
+            while c in used:
+                c += 1
+            tentative[v] = c
+        current = dict(final)
+        current.update(tentative)
+        losers = {v for v in todo
+                  if any(current[u] == tentative[v] and key(u) > key(v) for u in S[v])}
+        for v in todo - losers:
+            final[v] = tentative[v]
+        todo = losers
+    colors = [final[v] for v in range(n)]
+    return colors, len(sizes), max(colors, default=0), sizes
