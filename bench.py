@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: distance-1 coloring of an R-MAT scale-24 graph on GB300.
+
+One step = one full pgc_color_d1 call (degree setup, every speculate/detect
+round, color count) on a graph already resident in HBM.  Prints one JSON
+line.  `value` = edges colored per second (m = nnz / 2 undirected edges)
+over the device-timed steps; `e2e` = the same metric through the C ABI with
+pinned host buffers (H2D of the CSR and D2H of the colors inside the timed
+region).  `roofline` comes from the dominant kernel's CUDA-event time,
+measured in host-loop mode after the timed steps, against the algorithmic
+bytes of that kernel (worklists, offsets, adjacency, color gathers/writes).
+
+`--impl reference` times the CPU oracle (single thread) on a bounded sample
+(R-MAT scale 18 with the same generator parameters) instead.
+Multi-GPU (torchrun): independent replicas, one per rank ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEED = 1
+RMAT = dict(a=0.57, b=0.19, c=0.19)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes (per kernel, from the per-round trace)
+# --------------------------------------------------------------------------
+def d1_algorithmic_bytes(trace_w, trace_s, n):
+    """Bytes the method must move per kernel, from |W_r| and S_r = sum of
+    degrees over W_r (int32 everywhere):
+      assign (r >= 2): worklist 4|W| + offsets 8|W| + adjacency 4 S_r +
+                       color gathers 4 S_r + tentative write 4|W|
+      detect (r >= 1): worklist 4|W| + offsets 8|W| + own color 4|W| +
+                       adjacency 4 S_r + color gathers 4 S_r + commit 4|W| +
+                       append 4|W_{r+1}|
+      init: offsets 4(n+1) + degree and color writes 8n + worklist 4n
+    Degree and hash reads for equal-colored neighbors are not counted."""
+    w = np.asarray(trace_w, dtype=np.float64)
+    s = np.asarray(trace_s, dtype=np.float64)
+    nxt = np.append(w[1:], 0.0)
+    assign = float(np.sum(16 * w[1:] + 8 * s[1:]))
+    detect = float(np.sum(20 * w + 8 * s + 4 * nxt))
+    init = 4.0 * (n + 1) + 12.0 * n
+    return {"d1_assign": assign, "d1_detect": detect, "d1_init": init}
+
+
+# --------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_info():
+    model = None
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu model")):
+                model = l.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
+def oracle_edges_per_s(scale: int, repeats: int = 1):
+    """The CPU oracle as it stands, single-threaded, on R-MAT(scale)."""
+    import oracle
+    from paper_2107_00075_gb300 import inputs
+    g = inputs.rmat(scale, 16, seed=SEED, **RMAT)
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return (g.nnz / 2) / best, best, g
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on the host cores, bounded sample/step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2107_00075_gb300 import inputs
+    scale = args.reference_scale
+    g = inputs.rmat(scale, 16, seed=SEED, **RMAT)
+    for _ in range(args.warmup):
+        oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * (g.nnz / 2) / total
+    out = {
+        "impl": "reference", "metric": "edges colored/s (D1, RMAT scale 24)", "value": value,
+        "unit": "edges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "D1 R-MAT scale 24 (sampled: scale %d per step)" % scale,
+                   "n": g.n, "nnz": g.nnz, "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"R-MAT scale {scale}, edge factor 16 (1/{2**(24-scale)} of "
+                                   f"the workload), full coloring per step", **cpu_info()},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--reference-scale", type=int, default=18)
+    ap.add_argument("--cpu-baseline-scale", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2107_00075_gb300 as pgc
+    from paper_2107_00075_gb300 import inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- input (identical on every replica) ----
+    t0 = time.time()
+    g = inputs.rmat(args.scale, args.edge_factor, seed=SEED, **RMAT)
+    n, nnz = g.n, g.nnz
+    m = nnz // 2
+    log(f"[rank {rank}] R-MAT scale {args.scale}: n={n} nnz={nnz} gen {time.time()-t0:.1f}s")
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    colors = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream)
+
+    res = None
+    for _ in range(args.warmup):
+        res = step()
+    rounds, ncolors = res.rounds, res.num_colors
+
+    # ---- device-timed steps (inputs resident; 2.1 GB CSR > L2) ----
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * m / (ms_per_step / 1000.0)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+        h_ci = torch.from_numpy(g.col_idx).pin_memory()
+        h_col = torch.empty(n, dtype=torch.int32).pin_memory()
+        a_rp, a_ci, a_col = h_rp.numpy(), h_ci.numpy(), h_col.numpy()
+        pgc.pgc_color_d1(a_rp, a_ci, seed=SEED, colors=a_col)  # warm the staging buffers
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e_steps = max(1, min(args.steps, 5))
+        for _ in range(e_steps):
+            pgc.pgc_color_d1(a_rp, a_ci, seed=SEED, colors=a_col)
+        dt = (time.perf_counter() - t0) / e_steps
+        barrier()
+        assert np.array_equal(a_col, colors.cpu().numpy()), "host-staged colors differ"
+        e2e = {"value": world * m / dt, "unit": "edges/s",
+               "h2d_bytes_per_step": int(4 * (n + 1) + 4 * nnz),
+               "d2h_bytes_per_step": int(4 * n), "ms_per_step": 1000 * dt}
+
+    # ---- roofline of the dominant kernel (host-loop mode, CUDA events) ----
+    roofline = None
+    kernels = {}
+    peak, peak_kind = load_peaks()
+    if not args.no_profile:
+        prof = pgc.Profile(trace_cap=1 << 16)
+        pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
+                         flags=pgc.PGC_HOST_LOOP, profile=prof)
+        nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, n)
+        for name, kms in prof.kernel_ms.items():
+            kernels[name] = {"ms": kms, "launches": prof.kernel_launches[name],
+                             "alg_bytes": nbytes.get(name)}
+        top = max(prof.kernel_ms, key=prof.kernel_ms.get)
+        launches = prof.kernel_launches[top]
+        avg_s = prof.kernel_ms[top] / 1000.0 / launches
+        per_launch = nbytes[top] / launches
+        achieved = per_launch / avg_s / 1e9
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            tr = json.load(open(tpath)).get(top)
+            if tr and tr.get("workload") == f"rmat{args.scale}":
+                traffic = tr.get("bytes_per_launch")
+        roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+                    "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1000,
+                    "launches": launches}
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        eps, secs, sg = oracle_edges_per_s(args.cpu_baseline_scale)
+        cpu = {"value": eps, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"R-MAT scale {args.cpu_baseline_scale}, edge factor 16 "
+                         f"({sg.nnz} entries, 1/{2**(args.scale-args.cpu_baseline_scale)} of the "
+                         f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
+
+    if rank == 0:
+        launches_per_step = 2 * rounds  # init + round-1 detect + (assign, detect) per later round
+        out = {
+            "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"D1 R-MAT scale {args.scale}, edge factor {args.edge_factor}, "
+                                   "a=.57 b=.19 c=.19, symmetrized, dedup, no loops",
+                       "n": n, "nnz": nnz, "edges": m, "seed": SEED, "rounds": rounds,
+                       "num_colors": ncolors, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (CSR %.2f GB)" % ((4 * (n + 1 + nnz)) / 1e9)},
+            "nnz_per_s": value * 2, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * pgc.h -- C ABI of the GB300 speculative graph-coloring library.
+ *
+ * Computes distance-1 (D1), distance-2 (D2) and partial distance-2 (PD2)
+ * colorings by the speculate-and-resolve method of Bogle, Slota, Boman,
+ * Devine and Rajamanickam, "Parallel Graph Coloring Algorithms for
+ * Distributed GPU Environments" (arXiv 2107.00075), on one GPU:
+ *
+ *   round r: every vertex v on the worklist W_r takes the smallest color not
+ *   held by an already-colored vertex of its neighborhood S(v) (first fit,
+ *   Alg. 1); then each v in W_r checks S(v) for a vertex u holding the same
+ *   color with a higher priority, and if there is one v is uncolored and
+ *   goes to W_{r+1} (conflict detection, Alg. 3 for D1 and Alg. 5 for
+ *   D2/PD2; priority order of Alg. 4 with the recolorDegrees heuristic of
+ *   Sec. 3.3); otherwise v keeps its color.  The loop of Alg. 2 repeats
+ *   until the worklist is empty.
+ *
+ * Priority: key(v) = (deg(v), -h(v), -v) compared lexicographically, with
+ * h(v) = splitmix64(seed XOR v) as an unsigned 64-bit number.  So the
+ * lower-degree vertex of a conflict is recolored, on equal degree the one
+ * with the larger h, on equal h the one with the larger id (Alg. 4).
+ * deg(v) is the row length of the input (D1, D2) or the column length of
+ * the pattern (PD2), computed once (Sec. 3.3).  PGC_NO_DEGREE_RULE drops
+ * the degree term (the paper's "D1-baseline").
+ *
+ * The form is round-synchronous: within a round the first-fit step sees
+ * only colors committed in earlier rounds, and detection reads the round's
+ * colors as a snapshot.  The output is therefore a deterministic function
+ * of (graph, seed, flags): any launch configuration, batch composition or
+ * request mix gives the same colors.  Colors are 1..num_colors; every color
+ * in that range is used, and each vertex holds the smallest color absent
+ * from its neighborhood (a Grundy coloring).
+ *
+ * Memory: array arguments may be device memory (used in place) or host
+ * memory (staged through library-owned device buffers; the call then also
+ * copies the colors back).  The library never frees caller memory.  Scratch
+ * (degrees, worklists, masks, counters) is library-owned, allocated on
+ * first use per device and reused; pgc_release() frees it.
+ *
+ * Threads and streams: calls on one device are serialized by the library;
+ * `stream` (a cudaStream_t, NULL = the legacy default stream) orders the
+ * work after prior work on that stream.  Each call synchronizes `stream`
+ * before returning, because it returns rounds and num_colors by value.
+ *
+ * Errors: every entry point returns a pgc_status; on error the colors
+ * array is unspecified.  No C++ exception crosses this boundary.
+ * pgc_last_error() gives a message for the last error on the calling thread.
+ */
+#ifndef PGC_H
+#define PGC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGC_OK = 0,
+    PGC_ERR_INVALID_ARG = 1,   /* bad sizes/pointers, malformed CSR (PGC_VALIDATE) */
+    PGC_ERR_CUDA = 2,          /* a CUDA call failed; see pgc_last_error() */
+    PGC_ERR_OOM = 3,           /* device allocation failed */
+    PGC_ERR_NO_CONVERGE = 4,   /* max_rounds reached, or a round made no progress */
+    PGC_ERR_TIMEOUT = 5,       /* the device round loop ran past timeout_ms */
+    PGC_ERR_BUSY = 6,          /* server: admission refused (footprint over budget) */
+    PGC_ERR_NOT_FOUND = 7      /* server: unknown request id */
+} pgc_status;
+
+/* option flags */
+#define PGC_NO_DEGREE_RULE 0x1u  /* priority (-h(v), -v): Alg. 4 with recolorDegrees off */
+#define PGC_VALIDATE       0x2u  /* check CSR shape and ids before coloring */
+#define PGC_HOST_LOOP      0x4u  /* drive rounds from the host (one sync per round)
+                                    instead of the device-side graph loop; enables
+                                    per-kernel timing in pgc_profile */
+
+/* Per-kernel timing and per-round trace, filled when non-NULL in pgc_opts. */
+#define PGC_MAX_KERNELS 8
+typedef struct {
+    /* per-round trace: w[r] = |W_{r+1}|, s[r] = sum of deg over W_{r+1} */
+    int64_t *trace_w;          /* host array of trace_cap entries, or NULL */
+    int64_t *trace_s;          /* host array of trace_cap entries, or NULL */
+    int32_t trace_cap;
+    /* PGC_HOST_LOOP only: CUDA-event time per kernel (ms, summed over
+       launches) and launch counts; names in kernel_names[]. */
+    int32_t num_kernels;
+    double kernel_ms[PGC_MAX_KERNELS];
+    int64_t kernel_launches[PGC_MAX_KERNELS];
+    const char *kernel_names[PGC_MAX_KERNELS];
+} pgc_profile;
+
+typedef struct {
+    uint32_t flags;            /* PGC_* flags above */
+    int32_t max_rounds;        /* 0 => n + 1 (an upper bound: each round commits
+                                  the worklist vertex with the largest key) */
+    int32_t mid_degree;        /* 0 => default: vertices with deg > mid_degree use
+                                  a warp each */
+    int32_t hub_degree;        /* 0 => default: vertices with deg > hub_degree use
+                                  a thread block each */
+    int32_t block;             /* 0 => default threads per block (128..1024) */
+    int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
+    int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */
+    int32_t reserved;
+    pgc_profile *profile;      /* nullable */
+} pgc_opts;
+
+/* Initialise an options struct to defaults. */
+void pgc_opts_init(pgc_opts *opts);
+
+/*
+ * Distance-1 coloring (Sec. 2.1; Sec. 3.2 with Alg. 3 and 4).
+ *   n        number of vertices, >= 0
+ *   row_ptr  int32[n+1], CSR offsets, row_ptr[0] = 0, non-decreasing
+ *   col_idx  int32[row_ptr[n]], neighbor ids in [0, n); the graph must be
+ *            symmetric (u in N(v) iff v in N(u)); self-loops are skipped as
+ *            neighbors but count in the degree; duplicates count in the degree
+ *   seed     priority seed for h(v)
+ *   colors   int32[n], output, fully overwritten with 1..num_colors
+ *   rounds   host int32*, output: number of rounds executed (0 when n == 0)
+ *   num_colors host int32*, output: the largest color (0 when n == 0)
+ *   opts     nullable
+ *   stream   cudaStream_t or NULL
+ */
+pgc_status pgc_color_d1(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                        uint64_t seed, int32_t *colors, int32_t *rounds,
+                        int32_t *num_colors, const pgc_opts *opts, void *stream);
+
+/* Message for the last error on this thread ("" if none). */
+const char *pgc_last_error(void);
+
+/* Name of a status code. */
+const char *pgc_status_string(pgc_status s);
+
+/* Free library-owned device scratch on the current device. */
+pgc_status pgc_release(void);
+
+/* Library version string. */
+const char *pgc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGC_H */

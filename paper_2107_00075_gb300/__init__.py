@@ -1,1 +1,11 @@
-"""pgc -- GB300-native speculative graph coloring (D1, D2, PD2)."""
+"""pgc -- GB300-native speculative graph coloring (D1, D2, PD2).
+
+The computation lives in the CUDA library ``_build/libpgc.so`` (C ABI in
+``include/pgc.h``); ``binding`` marshals arguments to it.  Importing this
+package does not load the library; the first call does, and fails loudly if
+the library cannot be built or loaded.
+"""
+from .binding import (  # noqa: F401
+    PGC_HOST_LOOP, PGC_NO_DEGREE_RULE, PGC_VALIDATE, ColorResult, PgcError, Profile,
+    pgc_color_d1, pgc_release, pgc_version,
+)

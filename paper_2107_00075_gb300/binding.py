@@ -1,0 +1,214 @@
+"""Thin Python binding of the C ABI in include/pgc.h (argument marshalling only).
+
+Every computation runs in the CUDA library; these functions only turn torch
+tensors / numpy arrays into pointers, call the C entry point of the same
+name and raise on a non-OK status.  Arrays may live on the GPU (torch CUDA
+tensors, used in place) or on the host (numpy arrays or CPU tensors, staged
+by the library).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import _native
+
+PGC_OK = 0
+PGC_NO_DEGREE_RULE = 0x1
+PGC_VALIDATE = 0x2
+PGC_HOST_LOOP = 0x4
+PGC_MAX_KERNELS = 8
+
+STATUS_NAMES = {0: "PGC_OK", 1: "PGC_ERR_INVALID_ARG", 2: "PGC_ERR_CUDA", 3: "PGC_ERR_OOM",
+                4: "PGC_ERR_NO_CONVERGE", 5: "PGC_ERR_TIMEOUT", 6: "PGC_ERR_BUSY",
+                7: "PGC_ERR_NOT_FOUND"}
+
+
+class PgcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PgcProfileC(ctypes.Structure):
+    _fields_ = [("trace_w", ctypes.c_void_p), ("trace_s", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_int32), ("num_kernels", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_double * PGC_MAX_KERNELS),
+                ("kernel_launches", ctypes.c_int64 * PGC_MAX_KERNELS),
+                ("kernel_names", ctypes.c_char_p * PGC_MAX_KERNELS)]
+
+
+class PgcOptsC(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("max_rounds", ctypes.c_int32),
+                ("mid_degree", ctypes.c_int32), ("hub_degree", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("profile", ctypes.POINTER(PgcProfileC))]
+
+
+@dataclass
+class Profile:
+    """Per-round trace and (PGC_HOST_LOOP) per-kernel CUDA-event times."""
+    trace_cap: int = 4096
+    trace_w: np.ndarray = field(default=None)
+    trace_s: np.ndarray = field(default=None)
+    kernel_ms: dict = field(default_factory=dict)
+    kernel_launches: dict = field(default_factory=dict)
+
+
+@dataclass
+class ColorResult:
+    colors: object
+    rounds: int
+    num_colors: int
+
+
+_declared = False
+
+
+def lib():
+    """The loaded native library (raises if it cannot be built or loaded)."""
+    global _declared
+    L = _native.load()
+    if not _declared:
+        i32, u64, p = ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p
+        L.pgc_color_d1.argtypes = [i32, p, p, u64, p, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(PgcOptsC), p]
+        L.pgc_color_d1.restype = ctypes.c_int
+        L.pgc_last_error.restype = ctypes.c_char_p
+        L.pgc_status_string.argtypes = [ctypes.c_int]
+        L.pgc_status_string.restype = ctypes.c_char_p
+        L.pgc_version.restype = ctypes.c_char_p
+        L.pgc_release.restype = ctypes.c_int
+        L.pgc_opts_init.argtypes = [ctypes.POINTER(PgcOptsC)]
+        _declared = True
+    return L
+
+
+def _check(status: int):
+    if status != PGC_OK:
+        raise PgcError(status, lib().pgc_last_error().decode(errors="replace"))
+
+
+class _Arr:
+    """Pointer to an int32 array (torch tensor or numpy array), kept alive."""
+
+    def __init__(self, a, name):
+        self.obj = a
+        self.device = None
+        try:
+            import torch
+        except ImportError:  # pragma: no cover
+            torch = None
+        if torch is not None and isinstance(a, torch.Tensor):
+            if a.dtype != torch.int32 or not a.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous int32 tensor")
+            self.ptr = a.data_ptr()
+            self.device = a.device if a.is_cuda else None
+            self.n = a.numel()
+        else:
+            arr = np.asarray(a)
+            if arr.dtype != np.int32 or not arr.flags.c_contiguous:
+                raise TypeError(f"{name} must be a contiguous int32 array")
+            self.obj = arr
+            self.ptr = arr.ctypes.data
+            self.n = arr.size
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        if device is None:
+            return None
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm, timeout_ms,
+               profile: Optional[Profile]):
+    o = PgcOptsC()
+    lib().pgc_opts_init(ctypes.byref(o))
+    o.flags, o.max_rounds = flags, max_rounds
+    o.mid_degree, o.hub_degree = mid_degree, hub_degree
+    o.block, o.grid_per_sm, o.timeout_ms = block, grid_per_sm, timeout_ms
+    keep = []
+    if profile is not None:
+        pc = PgcProfileC()
+        profile.trace_w = np.zeros(profile.trace_cap, dtype=np.int64)
+        profile.trace_s = np.zeros(profile.trace_cap, dtype=np.int64)
+        pc.trace_w = profile.trace_w.ctypes.data
+        pc.trace_s = profile.trace_s.ctypes.data
+        pc.trace_cap = profile.trace_cap
+        o.profile = ctypes.pointer(pc)
+        keep.append(pc)
+    return o, keep
+
+
+def _finish_profile(profile: Optional[Profile], keep, rounds):
+    if profile is None:
+        return
+    pc = keep[0]
+    r = min(rounds, profile.trace_cap)
+    profile.trace_w = profile.trace_w[:r].copy()
+    profile.trace_s = profile.trace_s[:r].copy()
+    for k in range(pc.num_kernels):
+        name = pc.kernel_names[k]
+        if name:
+            profile.kernel_ms[name.decode()] = pc.kernel_ms[k]
+            profile.kernel_launches[name.decode()] = pc.kernel_launches[k]
+
+
+def _alloc_colors(n, device):
+    if device is None:
+        return np.zeros(n, dtype=np.int32)
+    import torch
+    return torch.empty(n, dtype=torch.int32, device=device)
+
+
+def _device_ctx(device):
+    import contextlib
+    if device is None:
+        return contextlib.nullcontext()
+    import torch
+    return torch.cuda.device(device)
+
+
+def pgc_color_d1(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0,
+                 max_rounds: int = 0, mid_degree: int = 0, hub_degree: int = 0,
+                 block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
+                 profile: Optional[Profile] = None, stream=None) -> ColorResult:
+    """Distance-1 coloring of a symmetric int32 CSR graph (see pgc.h)."""
+    rp = _Arr(row_ptr, "row_ptr")
+    ci = _Arr(col_idx, "col_idx")
+    n = rp.n - 1
+    if n < 0:
+        raise ValueError("row_ptr must have n + 1 >= 1 entries")
+    if colors is None:
+        colors = _alloc_colors(n, rp.device)
+    co = _Arr(colors, "colors")
+    if co.n < n:
+        raise ValueError("colors is shorter than n")
+    o, keep = _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm,
+                         timeout_ms, profile)
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    dev = rp.device or co.device
+    with _device_ctx(dev):
+        st = lib().pgc_color_d1(n, rp.ptr, ci.ptr if ci.n else None, ctypes.c_uint64(seed),
+                                co.ptr, ctypes.byref(rounds), ctypes.byref(ncol),
+                                ctypes.byref(o), _stream_handle(stream, dev))
+    _check(st)
+    _finish_profile(profile, keep, rounds.value)
+    return ColorResult(colors, rounds.value, ncol.value)
+
+
+def pgc_release():
+    _check(lib().pgc_release())
+
+
+def pgc_version() -> str:
+    return lib().pgc_version().decode()

@@ -1,0 +1,77 @@
+// runtime.h -- host-side internals of the coloring library (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pgc.h"
+
+namespace pgc {
+
+// Records msg as the calling thread's last error and returns s.
+pgc_status fail(pgc_status s, const std::string& msg);
+pgc_status cuda_fail(cudaError_t e, const char* what);
+
+#define PGC_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t e__ = (call);                                \
+        if (e__ != cudaSuccess) return ::pgc::cuda_fail(e__, #call); \
+    } while (0)
+
+// A device allocation that grows on demand and is reused across calls.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    pgc_status ensure(size_t need);   // grows (never shrinks); contents lost on growth
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Pinned host staging buffer.
+struct HostBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    pgc_status ensure(size_t need);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// true if p is host memory the GPU must not dereference (pageable or pinned
+// host allocation); false for device or managed memory.
+bool is_host_pointer(const void* p);
+
+// Effective options (defaults filled in).
+struct Opts {
+    uint32_t flags = 0;
+    int32_t max_rounds = 0;
+    int32_t mid_degree = 32;
+    int32_t hub_degree = 1024;
+    int32_t block = 256;
+    int32_t grid_per_sm = 0;
+    int32_t timeout_ms = 60000;
+    pgc_profile* profile = nullptr;
+};
+pgc_status read_opts(const pgc_opts* in, Opts* out);
+
+// Device properties cached per device.
+struct DeviceInfo {
+    int device = 0;
+    int num_sms = 0;
+};
+pgc_status current_device(DeviceInfo* out);
+
+// Times kernels with CUDA events in host-loop mode.
+struct KernelTimer {
+    pgc_profile* prof = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int slot = -1;
+    pgc_status begin(int slot, const char* name);
+    pgc_status end();
+    void destroy();
+};
+
+}  // namespace pgc
