@@ -100,23 +100,32 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # algorithmic bytes (per kernel, from the per-round trace)
 # --------------------------------------------------------------------------
-def d1_algorithmic_bytes(trace_w, trace_s, n):
-    """Bytes the method must move per kernel, from |W_r| and S_r = sum of
-    degrees over W_r (int32 everywhere):
-      assign (r >= 2): worklist 4|W| + offsets 8|W| + adjacency 4 S_r +
-                       color gathers 4 S_r + tentative write 4|W|
-      detect (r >= 1): worklist 4|W| + offsets 8|W| + own color 4|W| +
-                       adjacency 4 S_r + color gathers 4 S_r + commit 4|W| +
-                       append 4|W_{r+1}|
-      init: offsets 4(n+1) + degree and color writes 8n + worklist 4n
-    Degree and hash reads for equal-colored neighbors are not counted."""
+def d1_algorithmic_bytes(trace_w, trace_h, n, nnz, deg):
+    """Bytes each kernel must move for one coloring (int32 everywhere),
+    from |W_r| and H_r = sum over W_r of |H(v)| (the per-round scan lists):
+      classify: offsets 4(n+1) + degree, color and worklist writes 12n +
+                bitmap clear 4(nnz/32 + n)
+      build:    worklist 4n + offsets 8n + adjacency 4 nnz + neighbor degree
+                4 nnz + H lists 4 H_1 + list lengths 4n + worklist 4n
+      assign (r >= 2): worklist, offset, degree, one bitmap word, color
+                write: 20 |W_r|
+      detect:   worklist, offset, list length, own color, commit/append:
+                20 |W_r| + H list entries and their colors 8 H_r (an upper
+                bound: a loser stops at its first conflict)
+      push:     per adjacency entry of a winner with degree > 32: neighbor id,
+                its color, its two offsets, one bitmap word: 20 B
+    """
     w = np.asarray(trace_w, dtype=np.float64)
-    s = np.asarray(trace_s, dtype=np.float64)
-    nxt = np.append(w[1:], 0.0)
-    assign = float(np.sum(16 * w[1:] + 8 * s[1:]))
-    detect = float(np.sum(20 * w + 8 * s + 4 * nxt))
-    init = 4.0 * (n + 1) + 12.0 * n
-    return {"d1_assign": assign, "d1_detect": detect, "d1_init": init}
+    hh = np.asarray(trace_h, dtype=np.float64)
+    deg = np.asarray(deg)
+    big = float(deg[deg > 32].sum())
+    return {
+        "d1_classify": 4.0 * (n + 1) + 12.0 * n + 4.0 * (nnz / 32 + n),
+        "d1_build": 16.0 * n + 8.0 * nnz + 4.0 * float(hh[0]) + 4.0 * n,
+        "d1_assign": float(np.sum(20 * w[1:])),
+        "d1_detect": float(np.sum(20 * w + 8 * hh)),
+        "d1_push": 20.0 * big,
+    }
 
 
 # --------------------------------------------------------------------------
@@ -296,7 +305,7 @@ def main():
         prof = pgc.Profile(trace_cap=1 << 16)
         pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
                          flags=pgc.PGC_HOST_LOOP, profile=prof)
-        nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, n)
+        nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_h, n, nnz, np.diff(g.row_ptr))
         for name, kms in prof.kernel_ms.items():
             kernels[name] = {"ms": kms, "launches": prof.kernel_launches[name],
                              "alg_bytes": nbytes.get(name)}
@@ -327,7 +336,7 @@ def main():
                          f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
 
     if rank == 0:
-        launches_per_step = 2 * rounds  # init + round-1 detect + (assign, detect) per later round
+        launches_per_step = 3 * rounds + 1  # classify, build, then (assign,) detect, push
         out = {
             "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

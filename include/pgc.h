@@ -76,9 +76,12 @@ typedef enum {
 /* Per-kernel timing and per-round trace, filled when non-NULL in pgc_opts. */
 #define PGC_MAX_KERNELS 8
 typedef struct {
-    /* per-round trace: w[r] = |W_{r+1}|, s[r] = sum of deg over W_{r+1} */
+    /* per-round trace, entry r describes round r+1's worklist W_{r+1}:
+       w[r] = |W_{r+1}|, s[r] = sum of deg(v), h[r] = sum of the lengths of
+       the detection lists (D1: neighbors with higher priority) */
     int64_t *trace_w;          /* host array of trace_cap entries, or NULL */
     int64_t *trace_s;          /* host array of trace_cap entries, or NULL */
+    int64_t *trace_h;          /* host array of trace_cap entries, or NULL */
     int32_t trace_cap;
     /* PGC_HOST_LOOP only: CUDA-event time per kernel (ms, summed over
        launches) and launch counts; names in kernel_names[]. */
@@ -92,10 +95,10 @@ typedef struct {
     uint32_t flags;            /* PGC_* flags above */
     int32_t max_rounds;        /* 0 => n + 1 (an upper bound: each round commits
                                   the worklist vertex with the largest key) */
-    int32_t mid_degree;        /* 0 => default: vertices with deg > mid_degree use
-                                  a warp each */
-    int32_t hub_degree;        /* 0 => default: vertices with deg > hub_degree use
-                                  a thread block each */
+    int32_t mid_degree;        /* 0 => 32: a vertex whose per-round scan list
+                                  (D1: neighbors with higher priority) is longer
+                                  gets a warp instead of a thread */
+    int32_t hub_degree;        /* 0 => 1024: longer lists get a thread block */
     int32_t block;             /* 0 => default threads per block (128..1024) */
     int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
     int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */

@@ -35,7 +35,7 @@ class PgcError(RuntimeError):
 
 class PgcProfileC(ctypes.Structure):
     _fields_ = [("trace_w", ctypes.c_void_p), ("trace_s", ctypes.c_void_p),
-                ("trace_cap", ctypes.c_int32), ("num_kernels", ctypes.c_int32),
+                ("trace_h", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("num_kernels", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * PGC_MAX_KERNELS),
                 ("kernel_launches", ctypes.c_int64 * PGC_MAX_KERNELS),
                 ("kernel_names", ctypes.c_char_p * PGC_MAX_KERNELS)]
@@ -55,6 +55,7 @@ class Profile:
     trace_cap: int = 4096
     trace_w: np.ndarray = field(default=None)
     trace_s: np.ndarray = field(default=None)
+    trace_h: np.ndarray = field(default=None)
     kernel_ms: dict = field(default_factory=dict)
     kernel_launches: dict = field(default_factory=dict)
 
@@ -141,8 +142,10 @@ def _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm, ti
         pc = PgcProfileC()
         profile.trace_w = np.zeros(profile.trace_cap, dtype=np.int64)
         profile.trace_s = np.zeros(profile.trace_cap, dtype=np.int64)
+        profile.trace_h = np.zeros(profile.trace_cap, dtype=np.int64)
         pc.trace_w = profile.trace_w.ctypes.data
         pc.trace_s = profile.trace_s.ctypes.data
+        pc.trace_h = profile.trace_h.ctypes.data
         pc.trace_cap = profile.trace_cap
         o.profile = ctypes.pointer(pc)
         keep.append(pc)
@@ -156,6 +159,7 @@ def _finish_profile(profile: Optional[Profile], keep, rounds):
     r = min(rounds, profile.trace_cap)
     profile.trace_w = profile.trace_w[:r].copy()
     profile.trace_s = profile.trace_s[:r].copy()
+    profile.trace_h = profile.trace_h[:r].copy()
     for k in range(pc.num_kernels):
         name = pc.kernel_names[k]
         if name:

@@ -39,3 +39,67 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
 
 }  // namespace pgc
+
+namespace pgc {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Warp-aggregated worklist append: lanes push (pred, v); a per-warp shared
+// buffer of 64 slots is flushed 32 entries at a time with one atomicAdd, so
+// list writes are coalesced and counter atomics are 32x fewer.  All 32
+// lanes must call wa_push / wa_flush together.
+struct WarpAppend {
+    int* buf;    // 64 ints of shared memory owned by this warp
+    int count;   // warp-uniform, < 32 between calls
+};
+
+__device__ __forceinline__ void wa_push(WarpAppend& a, bool pred, int v, int* out, int* out_cnt) {
+    const unsigned lane = lane_id();
+    const unsigned m = __ballot_sync(kFullMask, pred);
+    if (pred) a.buf[a.count + __popc(m & ((1u << lane) - 1u))] = v;
+    a.count += __popc(m);
+    __syncwarp();
+    if (a.count >= 32) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(out_cnt, 32);
+        base = __shfl_sync(kFullMask, base, 0);
+        out[base + lane] = a.buf[lane];
+        const int rem = a.count - 32;
+        const int tmp = (int)lane < rem ? a.buf[32 + lane] : 0;
+        __syncwarp();
+        if ((int)lane < rem) a.buf[lane] = tmp;
+        a.count = rem;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void wa_flush(WarpAppend& a, int* out, int* out_cnt) {
+    if (a.count == 0) return;
+    const unsigned lane = lane_id();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(out_cnt, a.count);
+    base = __shfl_sync(kFullMask, base, 0);
+    if ((int)lane < a.count) out[base + lane] = a.buf[lane];
+    a.count = 0;
+    __syncwarp();
+}
+
+__device__ __forceinline__ int warp_max(int x) {
+    for (int o = 16; o; o >>= 1) x = max(x, __shfl_xor_sync(kFullMask, x, o));
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
+    return x;
+}
+
+// Index of the first word of v's forbidden-color bitmap.  Vertex v owns
+// floor(deg(v)/32) + 1 words (bits for colors 1..deg(v)+1, enough because a
+// first-fit color never exceeds deg(v)+1); with offset floor(rp[v]/32) + v
+// consecutive vertices never overlap and the total is nnz/32 + n + 1 words.
+__device__ __forceinline__ long long bitmap_offset(int rp_v, int v) {
+    return (long long)(rp_v >> 5) + v;
+}
+
+}  // namespace pgc

@@ -96,9 +96,7 @@ pgc_status read_opts(const pgc_opts* in, Opts* out) {
         if (in->timeout_ms > 0) o.timeout_ms = in->timeout_ms;
         o.profile = in->profile;
     }
-    if (o.mid_degree > 63) return fail(PGC_ERR_INVALID_ARG, "mid_degree must be <= 63");
     if (o.hub_degree < o.mid_degree) o.hub_degree = o.mid_degree;
-    if (o.hub_degree > 8192) return fail(PGC_ERR_INVALID_ARG, "hub_degree must be <= 8192");
     *out = o;
     return PGC_OK;
 }

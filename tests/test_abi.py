@@ -47,7 +47,7 @@ def test_status_strings_and_version():
 def test_opts_struct_layout():
     # the ctypes mirror must match the C layout: 8 int32 fields then a pointer
     assert ctypes.sizeof(binding.PgcOptsC) == 8 * 4 + 8
-    assert binding.PgcProfileC.kernel_ms.offset == 8 + 8 + 4 + 4
+    assert binding.PgcProfileC.kernel_ms.offset == 8 + 8 + 8 + 4 + 4
 
 
 def test_host_argument_checks_without_gpu():
