@@ -101,30 +101,34 @@ class ClockSampler:
 # algorithmic bytes (per kernel, from the per-round trace)
 # --------------------------------------------------------------------------
 def d1_algorithmic_bytes(trace_w, trace_h, n, nnz, deg):
-    """Bytes each kernel must move for one coloring (int32 everywhere),
-    from |W_r| and H_r = sum over W_r of |H(v)| (the per-round scan lists):
-      classify: offsets 4(n+1) + degree, color and worklist writes 12n +
-                bitmap clear 4(nnz/32 + n)
+    """Bytes each kernel must move for one coloring (int32 ids and colors,
+    64-bit forbidden-color words), from |W_r| and H_r = sum over W_r of
+    |H(v)| (the per-round scan lists):
+      classify: offsets 4(n+1) + degree, color, list-length and two flag
+                writes 20n + forbidden word 8n + overflow bitmap clear
+                4 sum(deg/32 + 1 | deg >= 64) + worklist 4n
       build:    worklist 4n + offsets 8n + adjacency 4 nnz + neighbor degree
-                4 nnz + H lists 4 H_1 + list lengths 4n + worklist 4n
-      assign (r >= 2): worklist, offset, degree, one bitmap word, color
-                write: 20 |W_r|
+                4 nnz + H lists 4 H_1 + list lengths 4n
+      tier:     list lengths 4n + worklists 4n
+      assign (r >= 2): worklist 4 + forbidden word 8 + color write 4 = 16 |W_r|
       detect:   worklist, offset, list length, own color, commit/append:
-                20 |W_r| + H list entries and their colors 8 H_r (an upper
-                bound: a loser stops at its first conflict)
-      push:     per adjacency entry of a winner with degree > 32: neighbor id,
-                its color, its two offsets, one bitmap word: 20 B
+                20 |W_r| + H entries and their colors 8 H_r (upper bound: a
+                loser stops at its first conflict)
+      push:     per adjacency entry of a vertex of degree > 32: neighbor id 4 +
+                forbidden-word update 8 = 12 B
     """
     w = np.asarray(trace_w, dtype=np.float64)
     hh = np.asarray(trace_h, dtype=np.float64)
     deg = np.asarray(deg)
     big = float(deg[deg > 32].sum())
+    ovf = float(((deg[deg >= 64] >> 5) + 1).sum())
     return {
-        "d1_classify": 4.0 * (n + 1) + 12.0 * n + 4.0 * (nnz / 32 + n),
-        "d1_build": 16.0 * n + 8.0 * nnz + 4.0 * float(hh[0]) + 4.0 * n,
-        "d1_assign": float(np.sum(20 * w[1:])),
+        "d1_classify": 4.0 * (n + 1) + 32.0 * n + 4.0 * ovf,
+        "d1_build": 16.0 * n + 8.0 * nnz + 4.0 * float(hh[0]),
+        "d1_tier": 8.0 * n,
+        "d1_assign": float(np.sum(16 * w[1:])),
         "d1_detect": float(np.sum(20 * w + 8 * hh)),
-        "d1_push": 20.0 * big,
+        "d1_push": 12.0 * big,
     }
 
 
@@ -336,7 +340,7 @@ def main():
                          f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
 
     if rank == 0:
-        launches_per_step = 3 * rounds + 1  # classify, build, then (assign,) detect, push
+        launches_per_step = 3 * rounds + 2  # classify, build, tier, then (assign,) detect, push
         out = {
             "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -17,20 +17,26 @@
 //     rounds -- have short lists.  A committed neighbor never holds v's
 //     tentative color (first fit excluded it), so v loses iff some u in H(v)
 //     currently holds v's tentative color.
-//   * First fit reads a per-vertex bitmap of forbidden colors (deg(v)+1
-//     bits).  When a vertex commits color c it sets bit c in the bitmaps of
-//     its still-uncolored neighbors ("push"); each edge is pushed at most
-//     once, so the total push work is one pass over the adjacency.
+//   * First fit reads a per-vertex set of forbidden colors: one 64-bit word
+//     for colors 1..64 and, for vertices of degree >= 64, an overflow bitmap
+//     up to color deg(v)+1 (a first-fit color never exceeds deg(v)+1).  When
+//     a vertex commits color c it sets bit c in its neighbors' sets ("push");
+//     each vertex pushes once, so the total push work is one pass over the
+//     adjacency.
 //
 // Color encoding in col[]: > 0 committed; < 0 tentative (-t) for a vertex
 // on the current worklist.  Every uncolored vertex is on the worklist, so
 // |col[u]| is u's current color during detection; a winner flips its own
 // sign in place without disturbing concurrent readers.
 //
-// Worklists are split by |H(v)| into tiers: S (one thread per vertex),
-// M (one warp), L (one thread block).  The round loop runs on the device: a
-// CUDA graph with a conditional WHILE node around {assign, detect, push};
-// the last block of detect updates the round state and sets the condition.
+// Work decomposition (no thread waits for another; no result depends on it):
+//   detect, by |H(v)|: S <= 16 one thread per vertex; M <= 128 one warp per
+//   vertex; longer lists are split into 128-entry items, one warp each, and
+//   the warp that finishes a vertex's last item decides for the vertex.
+//   push and setup split long adjacency lists into items the same way.
+// The round loop runs on the device: a CUDA graph with a conditional WHILE
+// node around {assign, detect, push}; the last block of detect updates the
+// round state and sets the loop condition.
 #include "runtime.h"
 #include "device_common.cuh"
 
@@ -45,9 +51,13 @@ std::vector<std::function<void()>>& release_hooks();
 
 namespace d1 {
 
-enum { TIER_S = 0, TIER_M = 1, TIER_L = 2, NTIER = 3 };
-constexpr int kPushChunk = 512;      // adjacency entries per push work item
-constexpr int kInlinePush = 32;      // S-tier winners up to this degree push inline
+// detect tiers by |H(v)|: up to det_s one thread; up to det_item one warp;
+// longer lists are cut into det_item-entry items (pgc_opts mid/hub_degree,
+// defaults 16 and 128)
+constexpr int kBuildS = 32;     // setup: degree up to this: one thread
+constexpr int kBuildM = 512;    // setup: degree up to this: one warp
+constexpr int kBuildItem = 512; // setup/push: adjacency items of this length
+constexpr int kInlinePush = 32; // S-tier winners up to this degree push inline
 
 enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3 };
 
@@ -56,12 +66,13 @@ struct State {
     int done;         // 1 once the loop has ended
     int status;       // ST_*
     int max_color;
-    int cnt[2][NTIER];          // detect worklist sizes, [parity][tier]
-    int cls_cnt[NTIER];         // setup: vertices per degree class
-    int push_cnt;               // push work items queued this round
-    unsigned blocks_done;       // last-block detection in detect
-    unsigned hub_next_build;    // dynamic indices for block-per-vertex work
-    unsigned hub_next_detect;
+    int ns[2];        // S-tier worklist sizes per parity
+    int nm[2];        // M-tier worklist sizes
+    int nc[2];        // C-tier work items
+    int ncv[2];       // C-tier vertices
+    int bs, bm, bc;   // setup: vertices (S, M) and items (C) per degree class
+    int push_cnt;     // push work items queued this round
+    unsigned blocks_done;
     int pad;
     unsigned long long s_next;  // sum of degrees of the next worklist
     unsigned long long h_next;  // sum of |H(v)| over the next worklist
@@ -75,11 +86,16 @@ struct Problem {
     int* col;
     int* deg;
     int* hlen;
-    int* hadj;          // H(v) stored at hadj[row_ptr[v] ...]
-    unsigned* bm;       // forbidden-color bitmaps
-    int* wl[2][NTIER];  // worklists by parity and tier; wl[0] doubles as the
-                        // degree classes during setup
-    int2* push_q;       // (vertex, chunk) push work items
+    int* hadj;                 // H(v) stored at hadj[row_ptr[v] ...]
+    unsigned long long* bm0;   // forbidden colors 1..64, one word per vertex
+    unsigned* bmx;             // forbidden colors 65..deg+1 (deg >= 64)
+    int* lose_flag;            // per vertex, for split H lists
+    int* done_cnt;             // per vertex, items finished this round
+    int* ws[2];                // S-tier worklists per parity
+    int* wm[2];                // M-tier worklists
+    int2* wc[2];               // C-tier (vertex, item) lists; wc[0] doubles as
+                               // the setup's long-degree item list
+    int2* push_q;              // (vertex, item) push work
     long long* trace_w;
     long long* trace_s;
     long long* trace_h;
@@ -89,14 +105,10 @@ struct Problem {
     int trace_cap;
     int n;
     int use_deg;
-    int mid;            // tier thresholds on list length (detect) / degree (setup)
-    int hub;
     int max_rounds;
+    int det_s;
+    int det_item;
 };
-
-__device__ __forceinline__ int tier_of(int d, int mid, int hub) {
-    return d <= mid ? TIER_S : (d <= hub ? TIER_M : TIER_L);
-}
 
 // key(u) > key(v), hashing only when the degree term does not decide.
 __device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v,
@@ -107,43 +119,62 @@ __device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v
     return u < v;
 }
 
-// Set bit (c-1) in u's bitmap if u is still uncolored and c <= deg(u)+1.
+__device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Forbid color c for u.  Setting bits of an already-colored vertex is
+// harmless (its set is never read again), so colors 1..64 need no check and
+// the update is a fire-and-forget reduction.
 __device__ __forceinline__ void push_color(const Problem& P, int u, int c) {
-    if (P.col[u] >= 0) return;
+    if (c <= 64) {
+        atomicOr(P.bm0 + u, 1ull << (c - 1));
+        return;
+    }
     const int ru = __ldg(P.row_ptr + u), du = __ldg(P.row_ptr + u + 1) - ru;
-    if (c - 1 > du) return;
-    atomicOr(P.bm + bitmap_offset(ru, u) + ((c - 1) >> 5), 1u << ((c - 1) & 31));
+    if (c - 1 > du) return;   // u's own first fit never reaches c
+    const int b = c - 65;
+    atomicOr(P.bmx + bitmap_offset(ru, u) + (b >> 5), 1u << (b & 31));
 }
 
 // ---------------------------------------------------------------------------
-// setup 1: degrees, tentative color 1, empty bitmaps, degree classes
+// setup 1: degrees, tentative color 1, empty forbidden sets, degree classes
 // ---------------------------------------------------------------------------
 __global__ void d1_classify(const Problem* __restrict__ Pp) {
     extern __shared__ int smem[];
     const Problem& P = *Pp;
     State* st = P.st;
     const int warp = threadIdx.x >> 5;
-    WarpAppend app[NTIER];
-    for (int t = 0; t < NTIER; ++t) app[t] = {smem + (warp * NTIER + t) * 64, 0};
+    WarpAppend as = {smem + warp * 128, 0}, am = {smem + warp * 128 + 64, 0};
     const int n = P.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
          wbase += stride) {
         const long long i = wbase + lane_id();
         const bool valid = i < n;
-        int t = -1;
+        int d = -1;
         if (valid) {
-            const int r0 = __ldg(P.row_ptr + i), d = __ldg(P.row_ptr + i + 1) - r0;
+            const int r0 = __ldg(P.row_ptr + i);
+            d = __ldg(P.row_ptr + i + 1) - r0;
             P.deg[i] = d;
             P.col[i] = -1;
-            unsigned* b = P.bm + bitmap_offset(r0, (int)i);
-            for (int w = 0; w <= (d >> 5); ++w) b[w] = 0u;
-            t = tier_of(d, P.mid, P.hub);
+            P.hlen[i] = 0;
+            P.lose_flag[i] = 0;
+            P.done_cnt[i] = 0;
+            P.bm0[i] = 0ull;
+            if (d >= 64) {
+                unsigned* b = P.bmx + bitmap_offset(r0, (int)i);
+                for (int w = 0; w <= (d >> 5); ++w) b[w] = 0u;
+            }
+            if (d > kBuildM) {
+                const int nit = ceil_div(d, kBuildItem);
+                const int base = atomicAdd(&st->bc, nit);
+                for (int k = 0; k < nit; ++k) P.wc[0][base + k] = make_int2((int)i, k);
+            }
         }
-        for (int k = 0; k < NTIER; ++k)
-            wa_push(app[k], valid && t == k, (int)i, P.wl[0][k], &st->cls_cnt[k]);
+        wa_push(as, valid && d <= kBuildS, (int)i, P.ws[0], &st->bs);
+        wa_push(am, valid && d > kBuildS && d <= kBuildM, (int)i, P.wm[0], &st->bm);
     }
-    for (int k = 0; k < NTIER; ++k) wa_flush(app[k], P.wl[0][k], &st->cls_cnt[k]);
+    wa_flush(as, P.ws[0], &st->bs);
+    wa_flush(am, P.wm[0], &st->bm);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->round = 1;
         st->t0 = global_ns();
@@ -155,10 +186,9 @@ __global__ void d1_classify(const Problem* __restrict__ Pp) {
 }
 
 // ---------------------------------------------------------------------------
-// setup 2: H(v) lists and the round-1 worklists (tiered by |H(v)|)
+// setup 2: H(v) = neighbors with higher priority, stored at hadj[row_ptr[v]]
 // ---------------------------------------------------------------------------
 __global__ void d1_build(const Problem* __restrict__ Pp) {
-    extern __shared__ int smem[];
     const Problem& P = *Pp;
     State* st = P.st;
     const int* __restrict__ rp = P.row_ptr;
@@ -167,44 +197,38 @@ __global__ void d1_build(const Problem* __restrict__ Pp) {
     const unsigned long long seed = P.seed;
     const bool use_deg = P.use_deg != 0;
     const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int nS = st->cls_cnt[TIER_S], nM = st->cls_cnt[TIER_M], nL = st->cls_cnt[TIER_L];
+    const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+    const int nS = st->bs, nM = st->bm, nC = st->bc;
     unsigned long long my_h = 0ull;
-    __shared__ int s_idx, s_pos;
 
-    // large degree: one block per vertex
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_idx = nL > 0 ? (int)atomicAdd(&st->hub_next_build, 1u) : nL;
-            s_pos = 0;
-        }
-        __syncthreads();
-        const int i = s_idx;
-        if (i >= nL) break;
-        const int v = P.wl[0][TIER_L][i];
+    // long adjacency: one warp per 512-entry item; positions by atomicAdd
+    for (int q = gw; q < nC; q += nw) {
+        const int2 it = P.wc[0][q];
+        const int v = it.x;
         const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
         const uint64_t hv = prio_hash(seed, (uint32_t)v);
-        for (int e = threadIdx.x; e < d; e += blockDim.x) {
-            const int u = __ldg(ci + beg + e);
-            if (u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg))
-                P.hadj[beg + atomicAdd(&s_pos, 1)] = u;
+        const int e0 = it.y * kBuildItem, e1 = min(d, e0 + kBuildItem);
+        for (int base = e0; base < e1; base += 32) {
+            const int e = base + lane;
+            int u = -1;
+            bool keep = false;
+            if (e < e1) {
+                u = __ldg(ci + beg + e);
+                keep = u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg);
+            }
+            const unsigned m = __ballot_sync(kFullMask, keep);
+            if (m == 0u) continue;
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(P.hlen + v, __popc(m));
+            pos = __shfl_sync(kFullMask, pos, 0);
+            if (keep) P.hadj[beg + pos + __popc(m & ((1u << lane) - 1u))] = u;
+            if (lane == 0) my_h += (unsigned long long)__popc(m);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int hl = s_pos;
-            P.hlen[v] = hl;
-            const int k = tier_of(hl, P.mid, P.hub);
-            P.wl[1][k][atomicAdd(&st->cnt[1][k], 1)] = v;
-            my_h += (unsigned long long)hl;
-        }
-        __syncthreads();
     }
 
-    WarpAppend app[NTIER];
-    for (int t = 0; t < NTIER; ++t) app[t] = {smem + (warp * NTIER + t) * 64, 0};
-
     // medium degree: one warp per vertex, ordered compaction by ballot
-    for (int i = blockIdx.x * wpb + warp; i < nM; i += gridDim.x * wpb) {
-        const int v = P.wl[0][TIER_M][i];
+    for (int i = gw; i < nM; i += nw) {
+        const int v = P.wm[0][i];
         const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
         const uint64_t hv = prio_hash(seed, (uint32_t)v);
         int pos = 0;
@@ -224,42 +248,86 @@ __global__ void d1_build(const Problem* __restrict__ Pp) {
             P.hlen[v] = pos;
             my_h += (unsigned long long)pos;
         }
-        const int k = tier_of(pos, P.mid, P.hub);
-        for (int t = 0; t < NTIER; ++t)
-            wa_push(app[t], lane == 0 && k == t, v, P.wl[1][t], &st->cnt[1][t]);
     }
 
     // small degree: one thread per vertex
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < nS;
-         wbase += stride) {
-        const long long i = wbase + lane;
-        int k = -1, v = -1;
-        if (i < nS) {
-            v = P.wl[0][TIER_S][i];
-            const int beg = __ldg(rp + v), end = __ldg(rp + v + 1), d = end - beg;
-            const uint64_t hv = prio_hash(seed, (uint32_t)v);
-            int pos = beg;
-            for (int e = beg; e < end; ++e) {
-                const int u = __ldg(ci + e);
-                if (u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg)) P.hadj[pos++] = u;
-            }
-            const int hl = pos - beg;
-            P.hlen[v] = hl;
-            my_h += (unsigned long long)hl;
-            k = tier_of(hl, P.mid, P.hub);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += stride) {
+        const int v = P.ws[0][i];
+        const int beg = __ldg(rp + v), end = __ldg(rp + v + 1), d = end - beg;
+        const uint64_t hv = prio_hash(seed, (uint32_t)v);
+        int pos = beg;
+        for (int e = beg; e < end; ++e) {
+            const int u = __ldg(ci + e);
+            if (u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg)) P.hadj[pos++] = u;
         }
-        for (int t = 0; t < NTIER; ++t)
-            wa_push(app[t], k == t, v, P.wl[1][t], &st->cnt[1][t]);
+        P.hlen[v] = pos - beg;
+        my_h += (unsigned long long)(pos - beg);
     }
-    for (int t = 0; t < NTIER; ++t) wa_flush(app[t], P.wl[1][t], &st->cnt[1][t]);
     my_h = warp_sum(my_h);
     if (lane == 0 && my_h) atomicAdd(&st->h_first, my_h);
 }
 
+// Append v to the worklist of its H-list tier (all 32 lanes call).
+struct TierAppend {
+    WarpAppend s, m;
+};
+
+__device__ __forceinline__ void tier_push(const Problem& P, TierAppend& a, bool pred, int v,
+                                          int hl, int p) {
+    State* st = P.st;
+    const bool c = pred && hl > P.det_item;
+    wa_push(a.s, pred && hl <= P.det_s, v, P.ws[p], &st->ns[p]);
+    wa_push(a.m, pred && hl > P.det_s && hl <= P.det_item, v, P.wm[p], &st->nm[p]);
+    if (c) {
+        const int nit = ceil_div(hl, P.det_item);
+        const int base = atomicAdd(&st->nc[p], nit);
+        for (int k = 0; k < nit; ++k) P.wc[p][base + k] = make_int2(v, k);
+        atomicAdd(&st->ncv[p], 1);
+    }
+}
+
 // ---------------------------------------------------------------------------
-// assign: first fit from the forbidden-color bitmap
+// setup 3: round-1 worklists by |H(v)|
 // ---------------------------------------------------------------------------
+__global__ void d1_tier(const Problem* __restrict__ Pp) {
+    extern __shared__ int smem[];
+    const Problem& P = *Pp;
+    const int warp = threadIdx.x >> 5;
+    TierAppend a = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
+    const int n = P.n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
+         wbase += stride) {
+        const long long i = wbase + lane_id();
+        const bool valid = i < n;
+        const int hl = valid ? P.hlen[i] : 0;
+        tier_push(P, a, valid, (int)i, hl, 1);
+    }
+    wa_flush(a.s, P.ws[1], &P.st->ns[1]);
+    wa_flush(a.m, P.wm[1], &P.st->nm[1]);
+}
+
+// ---------------------------------------------------------------------------
+// assign: first fit from the forbidden-color set
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void assign_one(const Problem& P, int v) {
+    const unsigned long long w0 = P.bm0[v];
+    int t;
+    if (w0 != ~0ull) {
+        t = __ffsll((long long)~w0);
+    } else {   // colors 1..64 all taken: deg(v) >= 64, scan the overflow bitmap
+        const int r0 = __ldg(P.row_ptr + v);
+        const int words = (__ldg(P.deg + v) >> 5) + 1;
+        const unsigned* b = P.bmx + bitmap_offset(r0, v);
+        int w = 0;
+        unsigned word = b[0];
+        while (word == kFullMask && w + 1 < words) word = b[++w];
+        t = 64 + w * 32 + __ffs(~word);
+    }
+    P.col[v] = -t;
+}
+
 __global__ void d1_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
                           int use_cond) {
     const Problem& P = *Pp;
@@ -271,19 +339,18 @@ __global__ void d1_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHa
         st->push_cnt = 0;   // the previous round's push kernel has finished
     }
     const int cp = *(volatile int*)&st->round & 1;
-    const int n0 = st->cnt[cp][TIER_S], n1 = st->cnt[cp][TIER_M], n2 = st->cnt[cp][TIER_L];
-    const int total = n0 + n1 + n2;
+    const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nc[cp];
+    const long long total = (long long)n0 + n1 + n2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int v = i < n0 ? P.wl[cp][TIER_S][i]
-                    : (i < n0 + n1 ? P.wl[cp][TIER_M][i - n0] : P.wl[cp][TIER_L][i - n0 - n1]);
-        const int r0 = __ldg(P.row_ptr + v);
-        const int words = (__ldg(P.deg + v) >> 5) + 1;
-        const unsigned* b = P.bm + bitmap_offset(r0, v);
-        int w = 0;
-        unsigned word = b[0];
-        while (word == kFullMask && w + 1 < words) word = b[++w];
-        P.col[v] = -(w * 32 + __ffs(~word));
+        if (i < n0) {
+            assign_one(P, P.ws[cp][i]);
+        } else if (i < n0 + n1) {
+            assign_one(P, P.wm[cp][i - n0]);
+        } else {
+            const int2 it = P.wc[cp][i - n0 - n1];
+            if (it.y == 0) assign_one(P, it.x);
+        }
     }
 }
 
@@ -294,11 +361,9 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
     State* st = P.st;
     const int r = st->round;
     const int cp = r & 1, np = cp ^ 1;
-    long long cur = 0, nxt = 0;
-    for (int k = 0; k < NTIER; ++k) {
-        cur += *(volatile int*)&st->cnt[cp][k];
-        nxt += *(volatile int*)&st->cnt[np][k];
-    }
+    const long long cur = (long long)st->ns[cp] + st->nm[cp] + st->ncv[cp];
+    const long long nxt = (long long)*(volatile int*)&st->ns[np] + *(volatile int*)&st->nm[np] +
+                          *(volatile int*)&st->ncv[np];
     if (r < P.trace_cap) {
         P.trace_w[r] = nxt;
         P.trace_s[r] = (long long)*(volatile unsigned long long*)&st->s_next;
@@ -319,24 +384,43 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
         status = ST_TIMEOUT;
     }
     if (!done) {
-        for (int k = 0; k < NTIER; ++k) st->cnt[cp][k] = 0;
+        st->ns[cp] = st->nm[cp] = st->nc[cp] = st->ncv[cp] = 0;
         st->round = r + 1;
         st->s_next = 0ull;
         st->h_next = 0ull;
     }
     st->status = status;
     st->done = done;
-    st->hub_next_detect = 0u;
     st->blocks_done = 0u;
     __threadfence();
     if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
-// Queue the push of v's color: ceil(deg/kPushChunk) work items.
+// Queue the push of v's color: ceil(deg / kBuildItem) work items.
 __device__ __forceinline__ void queue_push(const Problem& P, int v, int d) {
-    const int nch = (d + kPushChunk - 1) / kPushChunk;
-    const int base = atomicAdd(&P.st->push_cnt, nch);
-    for (int k = 0; k < nch; ++k) P.push_q[base + k] = make_int2(v, k);
+    const int nit = ceil_div(d, kBuildItem);
+    const int base = atomicAdd(&P.st->push_cnt, nit);
+    for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
+}
+
+// Warp-wide: does any of the H-list entries [e0, e1) of v (starting at
+// hadj[beg]) currently hold color t?  Four independent loads per lane.
+__device__ __forceinline__ bool warp_conflict(const Problem& P, int beg, int e0, int e1, int t) {
+    const int lane = lane_id();
+    bool hit = false;
+    for (int base = e0; base < e1; base += 128) {
+        int u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = base + j * 32 + lane;
+            u[j] = e < e1 ? __ldg(P.hadj + beg + e) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (u[j] >= 0 && abs(P.col[u[j]]) == t) hit = true;
+        if (__any_sync(kFullMask, hit)) return true;
+    }
+    return false;
 }
 
 __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
@@ -346,7 +430,7 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
     State* st = P.st;
     const int r = *(volatile int*)&st->round;
     const int cp = r & 1, np = cp ^ 1;
-    const int nS = st->cnt[cp][TIER_S], nM = st->cnt[cp][TIER_M], nL = st->cnt[cp][TIER_L];
+    const int nS = st->ns[cp], nM = st->nm[cp], nC = st->nc[cp];
     const int* __restrict__ rp = P.row_ptr;
     const int* __restrict__ ci = P.col_idx;
     const int* __restrict__ ha = P.hadj;
@@ -354,34 +438,34 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
     const int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
     int my_max = 0;
     unsigned long long my_s = 0ull, my_h = 0ull;
-    __shared__ int s_idx;
+    TierAppend app = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
 
-    // --- L tier: block per vertex (long H lists) ---
-    if (nL > 0) {
-        for (;;) {
-            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&st->hub_next_detect, 1u);
-            __syncthreads();
-            const int i = s_idx;
-            if (i >= nL) break;
-            const int v = P.wl[cp][TIER_L][i];
-            const int beg = __ldg(rp + v);
-            const int hl = P.hlen[v];
-            const int t = -col[v];
-            bool lose = false;
-            for (int base = 0; base < hl; base += blockDim.x) {
-                const int e = base + threadIdx.x;
-                const bool l = e < hl && abs(col[__ldg(ha + beg + e)]) == t;
-                if (__syncthreads_or(l)) {
-                    lose = true;
-                    break;
-                }
-            }
-            if (threadIdx.x == 0) {
+    // --- C tier: one warp per 128-entry item; the last item decides ---
+    for (int q = gw; q < nC; q += nw) {
+        const int2 it = P.wc[cp][q];
+        const int v = it.x;
+        const int hl = P.hlen[v];
+        const int nit = ceil_div(hl, P.det_item);
+        const int beg = __ldg(rp + v);
+        const int t = -col[v];
+        bool lose = false;
+        if (*(volatile int*)(P.lose_flag + v) == 0) {
+            const int e0 = it.y * P.det_item;
+            lose = warp_conflict(P, beg, e0, min(hl, e0 + P.det_item), t);
+        }
+        int last = 0, lost = 0;
+        if (lane == 0) {
+            if (lose) atomicOr(P.lose_flag + v, 1);
+            __threadfence();
+            last = atomicAdd(P.done_cnt + v, 1) == nit - 1;
+            if (last) {
+                lost = atomicExch(P.lose_flag + v, 0) != 0;
+                P.done_cnt[v] = 0;
                 const int d = __ldg(rp + v + 1) - beg;
-                if (lose) {
-                    P.wl[np][TIER_L][atomicAdd(&st->cnt[np][TIER_L], 1)] = v;
+                if (lost) {
                     my_s += (unsigned long long)d;
                     my_h += (unsigned long long)hl;
                 } else {
@@ -390,26 +474,19 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
                     queue_push(P, v, d);
                 }
             }
-            __syncthreads();
         }
+        last = __shfl_sync(kFullMask, last, 0);
+        lost = __shfl_sync(kFullMask, lost, 0);
+        tier_push(P, app, last && lost && lane == 0, v, hl, np);
     }
 
-    // --- M tier: warp per vertex ---
-    WarpAppend app = {smem + warp * 64, 0};
-    for (int i = blockIdx.x * wpb + warp; i < nM; i += gridDim.x * wpb) {
-        const int v = P.wl[cp][TIER_M][i];
+    // --- M tier: one warp per vertex ---
+    for (int i = gw; i < nM; i += nw) {
+        const int v = P.wm[cp][i];
         const int beg = __ldg(rp + v);
         const int hl = P.hlen[v];
         const int t = -col[v];
-        bool lose = false;
-        for (int base = 0; base < hl; base += 32) {
-            const int e = base + lane;
-            const bool l = e < hl && abs(col[__ldg(ha + beg + e)]) == t;
-            if (__any_sync(kFullMask, l)) {
-                lose = true;
-                break;
-            }
-        }
+        const bool lose = warp_conflict(P, beg, 0, hl, t);
         if (lane == 0) {
             const int d = __ldg(rp + v + 1) - beg;
             if (lose) {
@@ -421,27 +498,29 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
                 queue_push(P, v, d);
             }
         }
-        wa_push(app, lose && lane == 0, v, P.wl[np][TIER_M], &st->cnt[np][TIER_M]);
+        tier_push(P, app, lose && lane == 0, v, hl, np);
     }
-    wa_flush(app, P.wl[np][TIER_M], &st->cnt[np][TIER_M]);
 
-    // --- S tier: thread per vertex ---
+    // --- S tier: one thread per vertex ---
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < nS;
          wbase += stride) {
         const long long i = wbase + lane;
         bool lose = false;
-        int v = -1;
+        int v = -1, hl = 0;
         if (i < nS) {
-            v = P.wl[cp][TIER_S][i];
+            v = P.ws[cp][i];
             const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
-            const int hl = P.hlen[v];
+            hl = P.hlen[v];
             const int t = -col[v];
-            for (int e = 0; e < hl; ++e)
-                if (abs(col[__ldg(ha + beg + e)]) == t) {
-                    lose = true;
-                    break;
-                }
+            for (int e = 0; e < hl && !lose; e += 4) {
+                int u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (u[j] >= 0 && abs(col[u[j]]) == t) lose = true;
+            }
             if (lose) {
                 my_s += (unsigned long long)d;
                 my_h += (unsigned long long)hl;
@@ -458,9 +537,10 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
                 }
             }
         }
-        wa_push(app, lose, v, P.wl[np][TIER_S], &st->cnt[np][TIER_S]);
+        tier_push(P, app, lose, v, hl, np);
     }
-    wa_flush(app, P.wl[np][TIER_S], &st->cnt[np][TIER_S]);
+    wa_flush(app.s, P.ws[np], &st->ns[np]);
+    wa_flush(app.m, P.wm[np], &st->nm[np]);
 
     // --- per-warp totals ---
     my_max = warp_max(my_max);
@@ -488,7 +568,7 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
 }
 
 // ---------------------------------------------------------------------------
-// push: winners' colors into the bitmaps of uncolored neighbors
+// push: winners' colors into the forbidden sets of their neighbors
 // ---------------------------------------------------------------------------
 __global__ void d1_push(const Problem* __restrict__ Pp) {
     const Problem& P = *Pp;
@@ -499,10 +579,17 @@ __global__ void d1_push(const Problem* __restrict__ Pp) {
         const int v = item.x;
         const int c = P.col[v];
         const int r0 = __ldg(P.row_ptr + v), r1 = __ldg(P.row_ptr + v + 1);
-        const int beg = r0 + item.y * kPushChunk, end = min(beg + kPushChunk, r1);
-        for (int e = beg + lane; e < end; e += 32) {
-            const int u = __ldg(P.col_idx + e);
-            if (u != v) push_color(P, u, c);
+        const int beg = r0 + item.y * kBuildItem, end = min(beg + kBuildItem, r1);
+        for (int base = beg; base < end; base += 128) {
+            int u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = base + j * 32 + lane;
+                u[j] = e < end ? __ldg(P.col_idx + e) : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (u[j] >= 0 && u[j] != v) push_color(P, u[j], c);
         }
     }
 }
@@ -532,11 +619,10 @@ __global__ void d1_validate_ids(const int* __restrict__ rp, const int* __restric
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf deg, hlen, hadj, bm, wl, pushq, state, problem, trace, stage_rp, stage_ci, stage_col,
-        flag;
+    DevBuf deg, hlen, hadj, bm0, bmx, flags, ws, wm, wc, pushq, state, problem, trace, stage_rp,
+        stage_ci, stage_col, flag;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
-    // graph (valid for the launch geometry below)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
@@ -551,8 +637,8 @@ struct Context {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&deg, &hlen, &hadj, &bm, &wl, &pushq, &state, &problem, &trace,
-                          &stage_rp, &stage_ci, &stage_col, &flag})
+        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &flags, &ws, &wm, &wc, &pushq, &state,
+                          &problem, &trace, &stage_rp, &stage_ci, &stage_col, &flag})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
         trace_cap = 0;
@@ -592,20 +678,17 @@ static Context* get_context(int device) {
 
 struct Geometry {
     int grid, block;
-    size_t smem_setup, smem_detect;
+    size_t smem;   // two warp appenders per warp
 };
 
 static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
-    const int block = o.block;
-    const int wpb = block / 32;
-    g->block = block;
-    g->smem_setup = (size_t)wpb * NTIER * 64 * sizeof(int);
-    g->smem_detect = (size_t)wpb * 64 * sizeof(int);
+    g->block = o.block;
+    g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
     int per_sm = o.grid_per_sm;
     if (per_sm == 0) {
         int a = 0, b = 0;
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, d1_detect, block, g->smem_detect));
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, d1_build, block, g->smem_setup));
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, d1_detect, o.block, g->smem));
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, d1_build, o.block, 0));
         per_sm = std::max(1, std::min(a, b));
     }
     g->grid = cx.dev.num_sms * per_sm;
@@ -632,30 +715,32 @@ static pgc_status build_graph(Context& cx, const Geometry& g) {
     void* p_args[] = {&dP};
     void* c_args[] = {&dP, &hnd, &use_cond};
 
-    cudaGraphNode_t n_memset, n_cls, n_build, n_det1, n_push1, n_loop;
     cudaMemsetParams ms = {};
     ms.dst = cx.state.ptr;
     ms.value = 0;
     ms.elementSize = 4;
     ms.width = sizeof(State) / 4;
     ms.height = 1;
-    PGC_CUDA(cudaGraphAddMemsetNode(&n_memset, cx.graph, nullptr, 0, &ms));
-    cudaKernelNodeParams k_cls = knode((void*)d1_classify, g, g.smem_setup, p_args);
-    cudaKernelNodeParams k_build = knode((void*)d1_build, g, g.smem_setup, p_args);
-    cudaKernelNodeParams k_det = knode((void*)d1_detect, g, g.smem_detect, c_args);
+    cudaGraphNode_t n_ms, n_cls, n_build, n_tier, n_det, n_push, n_loop;
+    PGC_CUDA(cudaGraphAddMemsetNode(&n_ms, cx.graph, nullptr, 0, &ms));
+    cudaKernelNodeParams k_cls = knode((void*)d1_classify, g, g.smem, p_args);
+    cudaKernelNodeParams k_build = knode((void*)d1_build, g, 0, p_args);
+    cudaKernelNodeParams k_tier = knode((void*)d1_tier, g, g.smem, p_args);
+    cudaKernelNodeParams k_det = knode((void*)d1_detect, g, g.smem, c_args);
     cudaKernelNodeParams k_push = knode((void*)d1_push, g, 0, p_args);
     cudaKernelNodeParams k_asg = knode((void*)d1_assign, g, 0, c_args);
-    PGC_CUDA(cudaGraphAddKernelNode(&n_cls, cx.graph, &n_memset, 1, &k_cls));
+    PGC_CUDA(cudaGraphAddKernelNode(&n_cls, cx.graph, &n_ms, 1, &k_cls));
     PGC_CUDA(cudaGraphAddKernelNode(&n_build, cx.graph, &n_cls, 1, &k_build));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_det1, cx.graph, &n_build, 1, &k_det));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_push1, cx.graph, &n_det1, 1, &k_push));
+    PGC_CUDA(cudaGraphAddKernelNode(&n_tier, cx.graph, &n_build, 1, &k_tier));
+    PGC_CUDA(cudaGraphAddKernelNode(&n_det, cx.graph, &n_tier, 1, &k_det));
+    PGC_CUDA(cudaGraphAddKernelNode(&n_push, cx.graph, &n_det, 1, &k_push));
 
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cx.handle;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    PGC_CUDA(cudaGraphAddNode(&n_loop, cx.graph, &n_push1, nullptr, 1, &cp));
+    PGC_CUDA(cudaGraphAddNode(&n_loop, cx.graph, &n_push, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t b_asg, b_det, b_push;
     PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
@@ -671,15 +756,21 @@ static pgc_status build_graph(Context& cx, const Geometry& g) {
 static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const int* d_ci,
                       int* d_col, uint64_t seed, const Opts& o, cudaStream_t stream, int* rounds,
                       int* num_colors) {
-    // --- scratch (grows, never shrinks; pointers live in the Problem struct,
-    //     so the captured graph stays valid across calls) ---
-    const size_t bm_words = (size_t)(nnz >> 5) + (size_t)n + 1;
-    const size_t q_items = (size_t)n + (size_t)(nnz / kPushChunk) + 1;
+    // --- scratch (grows, never shrinks; pointers travel in the Problem
+    //     struct, so the captured graph stays valid across calls) ---
+    const size_t bmx_words = (size_t)(nnz >> 5) + (size_t)n + 1;
+    const size_t c_items = (size_t)n + (size_t)(nnz / o.hub_degree) + 1 +
+                           (size_t)(nnz / kBuildItem);
+    const size_t q_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
     if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hlen.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hadj.ensure((size_t)std::max<long long>(nnz, 1) * 4)) return s;
-    if (pgc_status s = cx.bm.ensure(bm_words * 4)) return s;
-    if (pgc_status s = cx.wl.ensure((size_t)n * 4 * 2 * NTIER)) return s;
+    if (pgc_status s = cx.bm0.ensure((size_t)n * 8)) return s;
+    if (pgc_status s = cx.bmx.ensure(bmx_words * 4)) return s;
+    if (pgc_status s = cx.flags.ensure((size_t)n * 8)) return s;
+    if (pgc_status s = cx.ws.ensure((size_t)n * 4 * 2)) return s;
+    if (pgc_status s = cx.wm.ensure((size_t)n * 4 * 2)) return s;
+    if (pgc_status s = cx.wc.ensure(c_items * sizeof(int2) * 2)) return s;
     if (pgc_status s = cx.pushq.ensure(q_items * sizeof(int2))) return s;
     if (pgc_status s = cx.state.ensure(sizeof(State))) return s;
     if (pgc_status s = cx.problem.ensure(sizeof(Problem))) return s;
@@ -704,10 +795,15 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     hp->deg = cx.deg.as<int>();
     hp->hlen = cx.hlen.as<int>();
     hp->hadj = cx.hadj.as<int>();
-    hp->bm = cx.bm.as<unsigned>();
-    int* wl = cx.wl.as<int>();
-    for (int p = 0; p < 2; ++p)
-        for (int k = 0; k < NTIER; ++k) hp->wl[p][k] = wl + (size_t)(p * NTIER + k) * n;
+    hp->bm0 = cx.bm0.as<unsigned long long>();
+    hp->bmx = cx.bmx.as<unsigned>();
+    hp->lose_flag = cx.flags.as<int>();
+    hp->done_cnt = cx.flags.as<int>() + n;
+    for (int p = 0; p < 2; ++p) {
+        hp->ws[p] = cx.ws.as<int>() + (size_t)p * n;
+        hp->wm[p] = cx.wm.as<int>() + (size_t)p * n;
+        hp->wc[p] = cx.wc.as<int2>() + (size_t)p * c_items;
+    }
     hp->push_q = cx.pushq.as<int2>();
     hp->trace_w = cx.trace.as<long long>();
     hp->trace_s = hp->trace_w + tcap;
@@ -718,9 +814,9 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     hp->timeout_ns = (unsigned long long)o.timeout_ms * 1000000ull;
     hp->n = n;
     hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
-    hp->mid = o.mid_degree;
-    hp->hub = o.hub_degree;
     hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
+    hp->det_s = o.mid_degree;
+    hp->det_item = o.hub_degree;
     PGC_CUDA(cudaMemcpyAsync(cx.problem.ptr, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
     Problem* dP = cx.problem.as<Problem>();
 
@@ -736,35 +832,29 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
         kt.stream = stream;
         const cudaGraphConditionalHandle none = 0;
         PGC_CUDA(cudaMemsetAsync(cx.state.ptr, 0, sizeof(State), stream));
-        if (pgc_status s = kt.begin(0, "d1_classify")) return s;
-        d1_classify<<<g.grid, g.block, g.smem_setup, stream>>>(dP);
-        PGC_CUDA(cudaGetLastError());
-        if (pgc_status s = kt.end()) return s;
-        if (pgc_status s = kt.begin(1, "d1_build")) return s;
-        d1_build<<<g.grid, g.block, g.smem_setup, stream>>>(dP);
-        PGC_CUDA(cudaGetLastError());
-        if (pgc_status s = kt.end()) return s;
+#define PGC_TIMED(slot, name, launch)                         \
+    do {                                                      \
+        if (pgc_status s_ = kt.begin(slot, name)) return s_;  \
+        launch;                                               \
+        PGC_CUDA(cudaGetLastError());                         \
+        if (pgc_status s_ = kt.end()) return s_;              \
+    } while (0)
+        PGC_TIMED(0, "d1_classify", (d1_classify<<<g.grid, g.block, g.smem, stream>>>(dP)));
+        PGC_TIMED(1, "d1_build", (d1_build<<<g.grid, g.block, 0, stream>>>(dP)));
+        PGC_TIMED(2, "d1_tier", (d1_tier<<<g.grid, g.block, g.smem, stream>>>(dP)));
         for (int round = 1;; ++round) {
-            if (round > 1) {
-                if (pgc_status s = kt.begin(2, "d1_assign")) return s;
-                d1_assign<<<g.grid, g.block, 0, stream>>>(dP, none, 0);
-                PGC_CUDA(cudaGetLastError());
-                if (pgc_status s = kt.end()) return s;
-            }
-            if (pgc_status s = kt.begin(3, "d1_detect")) return s;
-            d1_detect<<<g.grid, g.block, g.smem_detect, stream>>>(dP, none, 0);
-            PGC_CUDA(cudaGetLastError());
-            if (pgc_status s = kt.end()) return s;
-            if (pgc_status s = kt.begin(4, "d1_push")) return s;
-            d1_push<<<g.grid, g.block, 0, stream>>>(dP);
-            PGC_CUDA(cudaGetLastError());
-            if (pgc_status s = kt.end()) return s;
+            if (round > 1)
+                PGC_TIMED(3, "d1_assign", (d1_assign<<<g.grid, g.block, 0, stream>>>(dP, none, 0)));
+            PGC_TIMED(4, "d1_detect",
+                      (d1_detect<<<g.grid, g.block, g.smem, stream>>>(dP, none, 0)));
+            PGC_TIMED(5, "d1_push", (d1_push<<<g.grid, g.block, 0, stream>>>(dP)));
             PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
             PGC_CUDA(cudaStreamSynchronize(stream));
             if (hs->done) break;
             if (round > hp->max_rounds + 1)
                 return fail(PGC_ERR_CUDA, "device round control did not finish the loop");
         }
+#undef PGC_TIMED
         kt.destroy();
     }
     PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
