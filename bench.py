@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--dump-profile", default=None,
+                    help="write per-launch times and the per-round trace to this JSON file")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -306,9 +308,13 @@ def main():
     kernels = {}
     peak, peak_kind = load_peaks()
     if not args.no_profile:
-        prof = pgc.Profile(trace_cap=1 << 16)
+        prof = pgc.Profile(trace_cap=1 << 16, launch_cap=1 << 18)
         pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
                          flags=pgc.PGC_HOST_LOOP, profile=prof)
+        if args.dump_profile:
+            json.dump({"launches": prof.launches, "trace_w": prof.trace_w.tolist(),
+                       "trace_s": prof.trace_s.tolist(), "trace_h": prof.trace_h.tolist()},
+                      open(args.dump_profile, "w"))
         nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_h, n, nnz, np.diff(g.row_ptr))
         for name, kms in prof.kernel_ms.items():
             kernels[name] = {"ms": kms, "launches": prof.kernel_launches[name],

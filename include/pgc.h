@@ -89,6 +89,13 @@ typedef struct {
     double kernel_ms[PGC_MAX_KERNELS];
     int64_t kernel_launches[PGC_MAX_KERNELS];
     const char *kernel_names[PGC_MAX_KERNELS];
+    /* PGC_HOST_LOOP only, nullable: every timed launch in order, its kernel
+       slot and its time (ms); at most launch_cap entries are written and
+       num_launches counts them all. */
+    int32_t *launch_slot;
+    float *launch_ms;
+    int32_t launch_cap;
+    int32_t num_launches;
 } pgc_profile;
 
 typedef struct {
@@ -98,8 +105,7 @@ typedef struct {
     int32_t mid_degree;        /* 0 => 16: a vertex whose per-round scan list
                                   (D1: neighbors with higher priority) is longer
                                   gets a warp instead of a thread */
-    int32_t hub_degree;        /* 0 => 128: lists longer than this are cut into
-                                  items of this many entries, one warp each */
+    int32_t hub_degree;        /* 0 => 256: longer lists get a thread block */
     int32_t block;             /* 0 => default threads per block (128..1024) */
     int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
     int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */

@@ -38,7 +38,9 @@ class PgcProfileC(ctypes.Structure):
                 ("trace_h", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("num_kernels", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * PGC_MAX_KERNELS),
                 ("kernel_launches", ctypes.c_int64 * PGC_MAX_KERNELS),
-                ("kernel_names", ctypes.c_char_p * PGC_MAX_KERNELS)]
+                ("kernel_names", ctypes.c_char_p * PGC_MAX_KERNELS),
+                ("launch_slot", ctypes.c_void_p), ("launch_ms", ctypes.c_void_p),
+                ("launch_cap", ctypes.c_int32), ("num_launches", ctypes.c_int32)]
 
 
 class PgcOptsC(ctypes.Structure):
@@ -58,6 +60,8 @@ class Profile:
     trace_h: np.ndarray = field(default=None)
     kernel_ms: dict = field(default_factory=dict)
     kernel_launches: dict = field(default_factory=dict)
+    launch_cap: int = 0          # > 0: record every timed launch (host loop)
+    launches: list = field(default_factory=list)   # [(kernel name, ms)]
 
 
 @dataclass
@@ -147,6 +151,12 @@ def _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm, ti
         pc.trace_s = profile.trace_s.ctypes.data
         pc.trace_h = profile.trace_h.ctypes.data
         pc.trace_cap = profile.trace_cap
+        if profile.launch_cap > 0:
+            profile._slots = np.zeros(profile.launch_cap, dtype=np.int32)
+            profile._ms = np.zeros(profile.launch_cap, dtype=np.float32)
+            pc.launch_slot = profile._slots.ctypes.data
+            pc.launch_ms = profile._ms.ctypes.data
+            pc.launch_cap = profile.launch_cap
         o.profile = ctypes.pointer(pc)
         keep.append(pc)
     return o, keep
@@ -165,6 +175,11 @@ def _finish_profile(profile: Optional[Profile], keep, rounds):
         if name:
             profile.kernel_ms[name.decode()] = pc.kernel_ms[k]
             profile.kernel_launches[name.decode()] = pc.kernel_launches[k]
+    if profile.launch_cap > 0:
+        names = [(pc.kernel_names[k] or b"?").decode() for k in range(PGC_MAX_KERNELS)]
+        m = min(pc.num_launches, profile.launch_cap)
+        profile.launches = [(names[int(profile._slots[i])], float(profile._ms[i]))
+                            for i in range(m)]
 
 
 def _alloc_colors(n, device):

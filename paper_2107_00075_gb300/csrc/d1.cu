@@ -30,10 +30,11 @@
 // sign in place without disturbing concurrent readers.
 //
 // Work decomposition (no thread waits for another; no result depends on it):
-//   detect, by |H(v)|: S <= 16 one thread per vertex; M <= 128 one warp per
-//   vertex; longer lists are split into 128-entry items, one warp each, and
-//   the warp that finishes a vertex's last item decides for the vertex.
-//   push and setup split long adjacency lists into items the same way.
+//   detect, by |H(v)|: up to 16 entries one thread per vertex; up to 256 one
+//   warp per vertex; longer lists one thread block per vertex.  Every scan
+//   issues four independent loads per thread per step and a loser stops at
+//   the step that finds its conflict.  Setup and push cut long adjacency
+//   lists into 512-entry items, one warp each (no decision depends on them).
 // The round loop runs on the device: a CUDA graph with a conditional WHILE
 // node around {assign, detect, push}; the last block of detect updates the
 // round state and sets the loop condition.
@@ -51,9 +52,8 @@ std::vector<std::function<void()>>& release_hooks();
 
 namespace d1 {
 
-// detect tiers by |H(v)|: up to det_s one thread; up to det_item one warp;
-// longer lists are cut into det_item-entry items (pgc_opts mid/hub_degree,
-// defaults 16 and 128)
+// detect tiers by |H(v)|: up to det_s one thread; up to det_m one warp;
+// longer lists one block (pgc_opts mid/hub_degree, defaults 16 and 256)
 constexpr int kBuildS = 32;     // setup: degree up to this: one thread
 constexpr int kBuildM = 512;    // setup: degree up to this: one warp
 constexpr int kBuildItem = 512; // setup/push: adjacency items of this length
@@ -68,12 +68,11 @@ struct State {
     int max_color;
     int ns[2];        // S-tier worklist sizes per parity
     int nm[2];        // M-tier worklist sizes
-    int nc[2];        // C-tier work items
-    int ncv[2];       // C-tier vertices
+    int nl[2];        // L-tier worklist sizes
     int bs, bm, bc;   // setup: vertices (S, M) and items (C) per degree class
     int push_cnt;     // push work items queued this round
     unsigned blocks_done;
-    int pad;
+    unsigned l_next;  // dynamic index into the L-tier worklist
     unsigned long long s_next;  // sum of degrees of the next worklist
     unsigned long long h_next;  // sum of |H(v)| over the next worklist
     unsigned long long h_first; // sum of |H(v)| over all vertices
@@ -89,12 +88,10 @@ struct Problem {
     int* hadj;                 // H(v) stored at hadj[row_ptr[v] ...]
     unsigned long long* bm0;   // forbidden colors 1..64, one word per vertex
     unsigned* bmx;             // forbidden colors 65..deg+1 (deg >= 64)
-    int* lose_flag;            // per vertex, for split H lists
-    int* done_cnt;             // per vertex, items finished this round
     int* ws[2];                // S-tier worklists per parity
     int* wm[2];                // M-tier worklists
-    int2* wc[2];               // C-tier (vertex, item) lists; wc[0] doubles as
-                               // the setup's long-degree item list
+    int* wl[2];                // L-tier worklists
+    int2* items;               // setup: (vertex, item) list for long rows
     int2* push_q;              // (vertex, item) push work
     long long* trace_w;
     long long* trace_s;
@@ -107,7 +104,7 @@ struct Problem {
     int use_deg;
     int max_rounds;
     int det_s;
-    int det_item;
+    int det_m;
 };
 
 // key(u) > key(v), hashing only when the degree term does not decide.
@@ -157,8 +154,6 @@ __global__ void d1_classify(const Problem* __restrict__ Pp) {
             P.deg[i] = d;
             P.col[i] = -1;
             P.hlen[i] = 0;
-            P.lose_flag[i] = 0;
-            P.done_cnt[i] = 0;
             P.bm0[i] = 0ull;
             if (d >= 64) {
                 unsigned* b = P.bmx + bitmap_offset(r0, (int)i);
@@ -167,7 +162,7 @@ __global__ void d1_classify(const Problem* __restrict__ Pp) {
             if (d > kBuildM) {
                 const int nit = ceil_div(d, kBuildItem);
                 const int base = atomicAdd(&st->bc, nit);
-                for (int k = 0; k < nit; ++k) P.wc[0][base + k] = make_int2((int)i, k);
+                for (int k = 0; k < nit; ++k) P.items[base + k] = make_int2((int)i, k);
             }
         }
         wa_push(as, valid && d <= kBuildS, (int)i, P.ws[0], &st->bs);
@@ -203,7 +198,7 @@ __global__ void d1_build(const Problem* __restrict__ Pp) {
 
     // long adjacency: one warp per 512-entry item; positions by atomicAdd
     for (int q = gw; q < nC; q += nw) {
-        const int2 it = P.wc[0][q];
+        const int2 it = P.items[q];
         const int v = it.x;
         const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
         const uint64_t hv = prio_hash(seed, (uint32_t)v);
@@ -276,15 +271,9 @@ struct TierAppend {
 __device__ __forceinline__ void tier_push(const Problem& P, TierAppend& a, bool pred, int v,
                                           int hl, int p) {
     State* st = P.st;
-    const bool c = pred && hl > P.det_item;
     wa_push(a.s, pred && hl <= P.det_s, v, P.ws[p], &st->ns[p]);
-    wa_push(a.m, pred && hl > P.det_s && hl <= P.det_item, v, P.wm[p], &st->nm[p]);
-    if (c) {
-        const int nit = ceil_div(hl, P.det_item);
-        const int base = atomicAdd(&st->nc[p], nit);
-        for (int k = 0; k < nit; ++k) P.wc[p][base + k] = make_int2(v, k);
-        atomicAdd(&st->ncv[p], 1);
-    }
+    wa_push(a.m, pred && hl > P.det_s && hl <= P.det_m, v, P.wm[p], &st->nm[p]);
+    if (pred && hl > P.det_m) P.wl[p][atomicAdd(&st->nl[p], 1)] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -339,18 +328,13 @@ __global__ void d1_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHa
         st->push_cnt = 0;   // the previous round's push kernel has finished
     }
     const int cp = *(volatile int*)&st->round & 1;
-    const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nc[cp];
+    const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nl[cp];
     const long long total = (long long)n0 + n1 + n2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        if (i < n0) {
-            assign_one(P, P.ws[cp][i]);
-        } else if (i < n0 + n1) {
-            assign_one(P, P.wm[cp][i - n0]);
-        } else {
-            const int2 it = P.wc[cp][i - n0 - n1];
-            if (it.y == 0) assign_one(P, it.x);
-        }
+        const int v = i < n0 ? P.ws[cp][i]
+                    : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
+        assign_one(P, v);
     }
 }
 
@@ -361,9 +345,9 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
     State* st = P.st;
     const int r = st->round;
     const int cp = r & 1, np = cp ^ 1;
-    const long long cur = (long long)st->ns[cp] + st->nm[cp] + st->ncv[cp];
+    const long long cur = (long long)st->ns[cp] + st->nm[cp] + st->nl[cp];
     const long long nxt = (long long)*(volatile int*)&st->ns[np] + *(volatile int*)&st->nm[np] +
-                          *(volatile int*)&st->ncv[np];
+                          *(volatile int*)&st->nl[np];
     if (r < P.trace_cap) {
         P.trace_w[r] = nxt;
         P.trace_s[r] = (long long)*(volatile unsigned long long*)&st->s_next;
@@ -384,7 +368,7 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
         status = ST_TIMEOUT;
     }
     if (!done) {
-        st->ns[cp] = st->nm[cp] = st->nc[cp] = st->ncv[cp] = 0;
+        st->ns[cp] = st->nm[cp] = st->nl[cp] = 0;
         st->round = r + 1;
         st->s_next = 0ull;
         st->h_next = 0ull;
@@ -392,6 +376,7 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
     st->status = status;
     st->done = done;
     st->blocks_done = 0u;
+    st->l_next = 0u;
     __threadfence();
     if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
 }
@@ -430,7 +415,7 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
     State* st = P.st;
     const int r = *(volatile int*)&st->round;
     const int cp = r & 1, np = cp ^ 1;
-    const int nS = st->ns[cp], nM = st->nm[cp], nC = st->nc[cp];
+    const int nS = st->ns[cp], nM = st->nm[cp], nL = st->nl[cp];
     const int* __restrict__ rp = P.row_ptr;
     const int* __restrict__ ci = P.col_idx;
     const int* __restrict__ ha = P.hadj;
@@ -443,29 +428,39 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
     unsigned long long my_s = 0ull, my_h = 0ull;
     TierAppend app = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
 
-    // --- C tier: one warp per 128-entry item; the last item decides ---
-    for (int q = gw; q < nC; q += nw) {
-        const int2 it = P.wc[cp][q];
-        const int v = it.x;
-        const int hl = P.hlen[v];
-        const int nit = ceil_div(hl, P.det_item);
-        const int beg = __ldg(rp + v);
-        const int t = -col[v];
-        bool lose = false;
-        if (*(volatile int*)(P.lose_flag + v) == 0) {
-            const int e0 = it.y * P.det_item;
-            lose = warp_conflict(P, beg, e0, min(hl, e0 + P.det_item), t);
-        }
-        int last = 0, lost = 0;
-        if (lane == 0) {
-            if (lose) atomicOr(P.lose_flag + v, 1);
-            __threadfence();
-            last = atomicAdd(P.done_cnt + v, 1) == nit - 1;
-            if (last) {
-                lost = atomicExch(P.lose_flag + v, 0) != 0;
-                P.done_cnt[v] = 0;
+    // --- L tier: one block per vertex, 4 entries per thread per step ---
+    __shared__ int s_idx;
+    if (nL > 0) {
+        for (;;) {
+            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&st->l_next, 1u);
+            __syncthreads();
+            const int i = s_idx;
+            if (i >= nL) break;
+            const int v = P.wl[cp][i];
+            const int beg = __ldg(rp + v);
+            const int hl = P.hlen[v];
+            const int t = -col[v];
+            bool lose = false;
+            for (int base = 0; base < hl; base += 4 * blockDim.x) {
+                int u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = base + j * blockDim.x + threadIdx.x;
+                    u[j] = e < hl ? __ldg(ha + beg + e) : -1;
+                }
+                bool l = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (u[j] >= 0 && abs(col[u[j]]) == t) l = true;
+                if (__syncthreads_or(l)) {
+                    lose = true;
+                    break;
+                }
+            }
+            if (threadIdx.x == 0) {
                 const int d = __ldg(rp + v + 1) - beg;
-                if (lost) {
+                if (lose) {
+                    P.wl[np][atomicAdd(&st->nl[np], 1)] = v;
                     my_s += (unsigned long long)d;
                     my_h += (unsigned long long)hl;
                 } else {
@@ -474,10 +469,8 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
                     queue_push(P, v, d);
                 }
             }
+            __syncthreads();
         }
-        last = __shfl_sync(kFullMask, last, 0);
-        lost = __shfl_sync(kFullMask, lost, 0);
-        tier_push(P, app, last && lost && lane == 0, v, hl, np);
     }
 
     // --- M tier: one warp per vertex ---
@@ -619,7 +612,7 @@ __global__ void d1_validate_ids(const int* __restrict__ rp, const int* __restric
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf deg, hlen, hadj, bm0, bmx, flags, ws, wm, wc, pushq, state, problem, trace, stage_rp,
+    DevBuf deg, hlen, hadj, bm0, bmx, ws, wm, wl, items, pushq, state, problem, trace, stage_rp,
         stage_ci, stage_col, flag;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
@@ -637,7 +630,7 @@ struct Context {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &flags, &ws, &wm, &wc, &pushq, &state,
+        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &ws, &wm, &wl, &items, &pushq, &state,
                           &problem, &trace, &stage_rp, &stage_ci, &stage_col, &flag})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
@@ -759,18 +752,17 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     // --- scratch (grows, never shrinks; pointers travel in the Problem
     //     struct, so the captured graph stays valid across calls) ---
     const size_t bmx_words = (size_t)(nnz >> 5) + (size_t)n + 1;
-    const size_t c_items = (size_t)n + (size_t)(nnz / o.hub_degree) + 1 +
-                           (size_t)(nnz / kBuildItem);
+    const size_t b_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
     const size_t q_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
     if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hlen.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hadj.ensure((size_t)std::max<long long>(nnz, 1) * 4)) return s;
     if (pgc_status s = cx.bm0.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.bmx.ensure(bmx_words * 4)) return s;
-    if (pgc_status s = cx.flags.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.ws.ensure((size_t)n * 4 * 2)) return s;
     if (pgc_status s = cx.wm.ensure((size_t)n * 4 * 2)) return s;
-    if (pgc_status s = cx.wc.ensure(c_items * sizeof(int2) * 2)) return s;
+    if (pgc_status s = cx.wl.ensure((size_t)n * 4 * 2)) return s;
+    if (pgc_status s = cx.items.ensure(b_items * sizeof(int2))) return s;
     if (pgc_status s = cx.pushq.ensure(q_items * sizeof(int2))) return s;
     if (pgc_status s = cx.state.ensure(sizeof(State))) return s;
     if (pgc_status s = cx.problem.ensure(sizeof(Problem))) return s;
@@ -797,13 +789,12 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     hp->hadj = cx.hadj.as<int>();
     hp->bm0 = cx.bm0.as<unsigned long long>();
     hp->bmx = cx.bmx.as<unsigned>();
-    hp->lose_flag = cx.flags.as<int>();
-    hp->done_cnt = cx.flags.as<int>() + n;
     for (int p = 0; p < 2; ++p) {
         hp->ws[p] = cx.ws.as<int>() + (size_t)p * n;
         hp->wm[p] = cx.wm.as<int>() + (size_t)p * n;
-        hp->wc[p] = cx.wc.as<int2>() + (size_t)p * c_items;
+        hp->wl[p] = cx.wl.as<int>() + (size_t)p * n;
     }
+    hp->items = cx.items.as<int2>();
     hp->push_q = cx.pushq.as<int2>();
     hp->trace_w = cx.trace.as<long long>();
     hp->trace_s = hp->trace_w + tcap;
@@ -816,7 +807,7 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
     hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
     hp->det_s = o.mid_degree;
-    hp->det_item = o.hub_degree;
+    hp->det_m = o.hub_degree;
     PGC_CUDA(cudaMemcpyAsync(cx.problem.ptr, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
     Problem* dP = cx.problem.as<Problem>();
 

@@ -133,6 +133,11 @@ pgc_status KernelTimer::end() {
     PGC_CUDA(cudaEventElapsedTime(&ms, a, b));
     prof->kernel_ms[slot] += ms;
     prof->kernel_launches[slot] += 1;
+    const int k = prof->num_launches++;
+    if (k < prof->launch_cap) {
+        if (prof->launch_slot) prof->launch_slot[k] = slot;
+        if (prof->launch_ms) prof->launch_ms[k] = ms;
+    }
     slot = -1;
     return PGC_OK;
 }

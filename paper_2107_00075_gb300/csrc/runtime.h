@@ -48,7 +48,7 @@ struct Opts {
     uint32_t flags = 0;
     int32_t max_rounds = 0;
     int32_t mid_degree = 16;
-    int32_t hub_degree = 128;
+    int32_t hub_degree = 256;
     int32_t block = 256;
     int32_t grid_per_sm = 0;
     int32_t timeout_ms = 60000;

@@ -80,7 +80,7 @@ def test_stencil_32cubed(pgc):
     assert_parity(pgc, g, seed=1)
 
 
-@pytest.mark.parametrize("mid,hub", [(0, 0), (1, 2), (2, 8), (4, 16), (63, 64), (8, 100000)])
+@pytest.mark.parametrize("mid,hub", [(0, 0), (1, 2), (2, 8), (4, 16), (63, 64), (8, 100000), (1000, 1000)])
 def test_rmat_all_tiers(pgc, mid, hub):
     """Skewed degrees with thresholds moved so that every tier (thread,
     warp, block per vertex) carries work, including hubs above 8192 colors'
