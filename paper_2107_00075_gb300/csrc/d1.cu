@@ -30,11 +30,13 @@
 // sign in place without disturbing concurrent readers.
 //
 // Work decomposition (no thread waits for another; no result depends on it):
-//   detect, by |H(v)|: up to 16 entries one thread per vertex; up to 256 one
-//   warp per vertex; longer lists one thread block per vertex.  Every scan
-//   issues four independent loads per thread per step and a loser stops at
-//   the step that finds its conflict.  Setup and push cut long adjacency
-//   lists into 512-entry items, one warp each (no decision depends on them).
+//   detect, by |H(v)|: up to 32 entries one thread per vertex; up to 1024
+//   one warp per vertex; longer lists one thread block per vertex.  Scans
+//   step through the list one entry per thread, loading the next step's ids
+//   while the current step's colors are gathered, and a loser stops at the
+//   step that finds its conflict.  Setup cuts long rows into 512-entry items
+//   and push into 128-entry items, one warp each (no decision depends on
+//   them).
 // The round loop runs on the device: a CUDA graph with a conditional WHILE
 // node around {assign, detect, push}; the last block of detect updates the
 // round state and sets the loop condition.
@@ -53,10 +55,11 @@ std::vector<std::function<void()>>& release_hooks();
 namespace d1 {
 
 // detect tiers by |H(v)|: up to det_s one thread; up to det_m one warp;
-// longer lists one block (pgc_opts mid/hub_degree, defaults 16 and 256)
+// longer lists one block (pgc_opts mid/hub_degree, defaults 32 and 1024)
+constexpr int kPushItem = 128;  // push: adjacency items of this length
 constexpr int kBuildS = 32;     // setup: degree up to this: one thread
 constexpr int kBuildM = 512;    // setup: degree up to this: one warp
-constexpr int kBuildItem = 512; // setup/push: adjacency items of this length
+constexpr int kBuildItem = 512; // setup: adjacency items of this length
 constexpr int kInlinePush = 32; // S-tier winners up to this degree push inline
 
 enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3 };
@@ -381,29 +384,24 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
     if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
-// Queue the push of v's color: ceil(deg / kBuildItem) work items.
+// Queue the push of v's color: ceil(deg / kPushItem) work items.
 __device__ __forceinline__ void queue_push(const Problem& P, int v, int d) {
-    const int nit = ceil_div(d, kBuildItem);
+    const int nit = ceil_div(d, kPushItem);
     const int base = atomicAdd(&P.st->push_cnt, nit);
     for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
 }
 
 // Warp-wide: does any of the H-list entries [e0, e1) of v (starting at
-// hadj[beg]) currently hold color t?  Four independent loads per lane.
+// hadj[beg]) currently hold color t?  32 entries per step; the ids of the
+// next step are loaded before this step's colors are compared.
 __device__ __forceinline__ bool warp_conflict(const Problem& P, int beg, int e0, int e1, int t) {
     const int lane = lane_id();
-    bool hit = false;
-    for (int base = e0; base < e1; base += 128) {
-        int u[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = base + j * 32 + lane;
-            u[j] = e < e1 ? __ldg(P.hadj + beg + e) : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (u[j] >= 0 && abs(P.col[u[j]]) == t) hit = true;
-        if (__any_sync(kFullMask, hit)) return true;
+    int nxt = e0 + lane < e1 ? __ldg(P.hadj + beg + e0 + lane) : -1;
+    for (int base = e0; base < e1; base += 32) {
+        const int u = nxt;
+        const int e = base + 32 + lane;
+        nxt = e < e1 ? __ldg(P.hadj + beg + e) : -1;
+        if (__any_sync(kFullMask, u >= 0 && abs(P.col[u]) == t)) return true;
     }
     return false;
 }
@@ -441,18 +439,12 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
             const int hl = P.hlen[v];
             const int t = -col[v];
             bool lose = false;
-            for (int base = 0; base < hl; base += 4 * blockDim.x) {
-                int u[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int e = base + j * blockDim.x + threadIdx.x;
-                    u[j] = e < hl ? __ldg(ha + beg + e) : -1;
-                }
-                bool l = false;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (u[j] >= 0 && abs(col[u[j]]) == t) l = true;
-                if (__syncthreads_or(l)) {
+            int nxt = (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
+            for (int base = 0; base < hl; base += blockDim.x) {
+                const int u = nxt;
+                const int e = base + blockDim.x + threadIdx.x;
+                nxt = e < hl ? __ldg(ha + beg + e) : -1;
+                if (__syncthreads_or(u >= 0 && abs(col[u]) == t)) {
                     lose = true;
                     break;
                 }
@@ -506,13 +498,14 @@ __global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHa
             const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
             hl = P.hlen[v];
             const int t = -col[v];
-            for (int e = 0; e < hl && !lose; e += 4) {
-                int u[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (u[j] >= 0 && abs(col[u[j]]) == t) lose = true;
+            int nxt = hl > 0 ? __ldg(ha + beg) : -1;
+            for (int e = 0; e < hl; ++e) {
+                const int u = nxt;
+                nxt = e + 1 < hl ? __ldg(ha + beg + e + 1) : -1;
+                if (abs(col[u]) == t) {
+                    lose = true;
+                    break;
+                }
             }
             if (lose) {
                 my_s += (unsigned long long)d;
@@ -572,7 +565,7 @@ __global__ void d1_push(const Problem* __restrict__ Pp) {
         const int v = item.x;
         const int c = P.col[v];
         const int r0 = __ldg(P.row_ptr + v), r1 = __ldg(P.row_ptr + v + 1);
-        const int beg = r0 + item.y * kBuildItem, end = min(beg + kBuildItem, r1);
+        const int beg = r0 + item.y * kPushItem, end = min(beg + kPushItem, r1);
         for (int base = beg; base < end; base += 128) {
             int u[4];
 #pragma unroll
@@ -753,7 +746,7 @@ static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const 
     //     struct, so the captured graph stays valid across calls) ---
     const size_t bmx_words = (size_t)(nnz >> 5) + (size_t)n + 1;
     const size_t b_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
-    const size_t q_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
+    const size_t q_items = (size_t)n + (size_t)(nnz / kPushItem) + 1;
     if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hlen.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.hadj.ensure((size_t)std::max<long long>(nnz, 1) * 4)) return s;
