@@ -134,6 +134,36 @@ pgc_status pgc_color_d1(int32_t n, const int32_t *row_ptr, const int32_t *col_id
                         uint64_t seed, int32_t *colors, int32_t *rounds,
                         int32_t *num_colors, const pgc_opts *opts, void *stream);
 
+/*
+ * Distance-2 coloring (Sec. 2.1; Sec. 3.5 with Alg. 5, doPartialColoring
+ * false): every two vertices joined by a path of one or two edges get
+ * different colors.  Arguments, layout and ownership as pgc_color_d1; the
+ * priority degree is the row length (1-hop degree).  Colors up to 4096 are
+ * supported (PGC_ERR_NO_CONVERGE beyond).  Detection is net based: the
+ * closed neighborhood N[u] of every vertex u is a net (Sec. 3.5, NB_BIT).
+ */
+pgc_status pgc_color_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                        uint64_t seed, int32_t *colors, int32_t *rounds,
+                        int32_t *num_colors, const pgc_opts *opts, void *stream);
+
+/*
+ * Partial distance-2 coloring of the columns of an n_rows x n_cols pattern
+ * (Sec. 2.1, Sec. 3.6; Alg. 5 with doPartialColoring true): two columns that
+ * have an entry in a common row get different colors; rows get no color.
+ *   row_ptr int32[n_rows+1], col_idx int32[nnz]  CSR of the pattern
+ *           (column ids in [0, n_cols))
+ *   col_ptr int32[n_cols+1], row_idx int32[nnz]  CSC of the same pattern
+ *           (row ids in [0, n_rows)); row_ptr[n_rows] must equal
+ *           col_ptr[n_cols], else PGC_ERR_INVALID_ARG
+ *   colors  int32[n_cols], output
+ * The priority degree of a column is its CSC length.  Colors up to 4096.
+ */
+pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_t *row_ptr,
+                         const int32_t *col_idx, const int32_t *col_ptr,
+                         const int32_t *row_idx, uint64_t seed, int32_t *colors,
+                         int32_t *rounds, int32_t *num_colors, const pgc_opts *opts,
+                         void *stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char *pgc_last_error(void);
 

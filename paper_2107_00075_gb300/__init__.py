@@ -7,5 +7,5 @@ the library cannot be built or loaded.
 """
 from .binding import (  # noqa: F401
     PGC_HOST_LOOP, PGC_NO_DEGREE_RULE, PGC_VALIDATE, ColorResult, PgcError, Profile,
-    pgc_color_d1, pgc_release, pgc_version,
+    pgc_color_d1, pgc_color_d2, pgc_color_pd2, pgc_release, pgc_version,
 )

@@ -83,6 +83,11 @@ def lib():
         L.pgc_color_d1.argtypes = [i32, p, p, u64, p, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_d1.restype = ctypes.c_int
+        L.pgc_color_d2.argtypes = L.pgc_color_d1.argtypes
+        L.pgc_color_d2.restype = ctypes.c_int
+        L.pgc_color_pd2.argtypes = [i32, i32, p, p, p, p, u64, p, ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), ctypes.POINTER(PgcOptsC), p]
+        L.pgc_color_pd2.restype = ctypes.c_int
         L.pgc_last_error.restype = ctypes.c_char_p
         L.pgc_status_string.argtypes = [ctypes.c_int]
         L.pgc_status_string.restype = ctypes.c_char_p
@@ -202,6 +207,49 @@ def pgc_color_d1(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0
                  block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
                  profile: Optional[Profile] = None, stream=None) -> ColorResult:
     """Distance-1 coloring of a symmetric int32 CSR graph (see pgc.h)."""
+    return _color_sym("pgc_color_d1", row_ptr, col_idx, seed, colors, flags, max_rounds,
+                      mid_degree, hub_degree, block, grid_per_sm, timeout_ms, profile, stream)
+
+
+def pgc_color_d2(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0,
+                 max_rounds: int = 0, mid_degree: int = 0, hub_degree: int = 0,
+                 block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
+                 profile: Optional[Profile] = None, stream=None) -> ColorResult:
+    """Distance-2 coloring of a symmetric int32 CSR graph (see pgc.h)."""
+    return _color_sym("pgc_color_d2", row_ptr, col_idx, seed, colors, flags, max_rounds,
+                      mid_degree, hub_degree, block, grid_per_sm, timeout_ms, profile, stream)
+
+
+def pgc_color_pd2(n_rows: int, n_cols: int, row_ptr, col_idx, col_ptr, row_idx,
+                  seed: int = 1, colors=None, *, flags: int = 0, max_rounds: int = 0,
+                  block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
+                  profile: Optional[Profile] = None, stream=None) -> ColorResult:
+    """Partial distance-2 coloring of the columns of a pattern given as CSR
+    and CSC (see pgc.h)."""
+    rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
+    cp, ri = _Arr(col_ptr, "col_ptr"), _Arr(row_idx, "row_idx")
+    if rp.n != n_rows + 1 or cp.n != n_cols + 1:
+        raise ValueError("row_ptr/col_ptr sizes do not match n_rows/n_cols")
+    if colors is None:
+        colors = _alloc_colors(n_cols, rp.device)
+    co = _Arr(colors, "colors")
+    if co.n < n_cols:
+        raise ValueError("colors is shorter than n_cols")
+    o, keep = _make_opts(flags, max_rounds, 0, 0, block, grid_per_sm, timeout_ms, profile)
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    dev = rp.device or co.device
+    with _device_ctx(dev):
+        st = lib().pgc_color_pd2(n_rows, n_cols, rp.ptr, ci.ptr if ci.n else None, cp.ptr,
+                                 ri.ptr if ri.n else None, ctypes.c_uint64(seed), co.ptr,
+                                 ctypes.byref(rounds), ctypes.byref(ncol), ctypes.byref(o),
+                                 _stream_handle(stream, dev))
+    _check(st)
+    _finish_profile(profile, keep, rounds.value)
+    return ColorResult(colors, rounds.value, ncol.value)
+
+
+def _color_sym(fname, row_ptr, col_idx, seed, colors, flags, max_rounds, mid_degree,
+               hub_degree, block, grid_per_sm, timeout_ms, profile, stream):
     rp = _Arr(row_ptr, "row_ptr")
     ci = _Arr(col_idx, "col_idx")
     n = rp.n - 1
@@ -217,7 +265,7 @@ def pgc_color_d1(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0
     rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
     dev = rp.device or co.device
     with _device_ctx(dev):
-        st = lib().pgc_color_d1(n, rp.ptr, ci.ptr if ci.n else None, ctypes.c_uint64(seed),
+        st = getattr(lib(), fname)(n, rp.ptr, ci.ptr if ci.n else None, ctypes.c_uint64(seed),
                                 co.ptr, ctypes.byref(rounds), ctypes.byref(ncol),
                                 ctypes.byref(o), _stream_handle(stream, dev))
     _check(st)

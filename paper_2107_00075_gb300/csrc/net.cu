@@ -1,0 +1,805 @@
+// net.cu -- distance-2 (D2) and partial distance-2 (PD2) coloring.
+//
+// Method (Bogle et al., Sec. 3.5-3.6, Alg. 5; first fit of Alg. 1, loser
+// order of Alg. 4), round-synchronous form as for D1.  Both problems are
+// written over "nets" (the net-based view of NB_BIT, Sec. 3.5): two vertices
+// must differ iff they are members of a common net.
+//   D2 : one net per vertex u, members N[u] = {u} + N(u); the nets of v are
+//        N[v]'s indices {v} + N(v).  Two vertices share a net iff they are
+//        within two hops (Sec. 2.1).
+//   PD2: the nets are the rows of the pattern, members are the row's
+//        columns (CSR); the nets of column v are its rows (CSC) (Sec. 3.6).
+// Only the vertices (D2) or columns (PD2) are colored.
+//
+// Per round:
+//   assign  v in W: forbidden(v) = OR of the color masks of v's nets;
+//           t = first free color (Alg. 1); col[v] = -t.  Marks v's nets
+//           active for this round.
+//   detect  one warp per active net: each uncolored member v whose color is
+//           also held by a member with priority loses (Alg. 5 + Alg. 4).
+//   commit  v in W: losers form W_{r+1}; a winner commits and sets bit t in
+//           the masks of its nets (so a mask is always the OR of its
+//           committed members' colors, kept incrementally: each vertex
+//           updates its nets once).
+// The loop runs on the device (CUDA graph, conditional WHILE node).
+#include "runtime.h"
+#include "device_common.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <unordered_map>
+
+namespace pgc {
+std::vector<std::function<void()>>& release_hooks();
+
+namespace net {
+
+constexpr int kThreadNets = 32;   // vertices with up to this many nets: one thread
+constexpr int kMaxWindows = 64;   // masks hold colors 1..64*windows (<= 4096)
+
+enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3, ST_OVERFLOW = 4 };
+
+struct State {
+    int round;
+    int done;
+    int status;
+    int max_color;
+    int nt[2];        // thread-tier worklist sizes per parity
+    int nw[2];        // warp-tier worklist sizes
+    int pad0;
+    unsigned blocks_done;
+    int bound;        // max over v of sum over its nets of (|net| - 1)
+    int pad;
+    unsigned long long s_next;
+    unsigned long long h_next;
+    unsigned long long h_first;
+    unsigned long long t0;
+};
+
+struct Problem {
+    const int* m_ptr;     // net -> members
+    const int* m_idx;
+    const int* r_ptr;     // vertex -> nets
+    const int* r_idx;
+    int* col;
+    int* deg;
+    int* lose;
+    int* net_flag;              // = round number while the net is active
+    unsigned long long* mask;   // [window][net]
+    int* wt[2];
+    int* ww[2];
+    long long* trace_w;
+    long long* trace_s;
+    long long* trace_h;
+    State* st;
+    unsigned long long seed;
+    unsigned long long timeout_ns;
+    int trace_cap;
+    int n;            // colored vertices
+    int n_nets;
+    int self;         // 1: D2 (net u contains u; v's nets include v's own)
+    int windows;
+    int use_deg;
+    int max_rounds;
+};
+
+// member j of net q (j < net_size)
+__device__ __forceinline__ int net_member(const Problem& P, int q, int j) {
+    if (P.self) return j == 0 ? q : __ldg(P.m_idx + __ldg(P.m_ptr + q) + j - 1);
+    return __ldg(P.m_idx + __ldg(P.m_ptr + q) + j);
+}
+__device__ __forceinline__ int net_size(const Problem& P, int q) {
+    return __ldg(P.m_ptr + q + 1) - __ldg(P.m_ptr + q) + P.self;
+}
+// k-th net of vertex v (k < nets_of_size)
+__device__ __forceinline__ int vertex_net(const Problem& P, int v, int beg, int k) {
+    if (P.self) return k == 0 ? v : __ldg(P.r_idx + beg + k - 1);
+    return __ldg(P.r_idx + beg + k);
+}
+
+__device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v,
+                                       unsigned long long seed, bool use_deg) {
+    if (use_deg && du != dv) return du > dv;
+    const uint64_t hu = prio_hash(seed, (uint32_t)u);
+    if (hu != hv) return hu < hv;
+    return u < v;
+}
+
+// ---------------------------------------------------------------------------
+// init: degrees, empty colors, worklists by number of nets, the color bound
+// ---------------------------------------------------------------------------
+__global__ void net_init(const Problem* __restrict__ Pp) {
+    extern __shared__ int smem[];
+    const Problem& P = *Pp;
+    State* st = P.st;
+    const int warp = threadIdx.x >> 5;
+    WarpAppend at = {smem + warp * 128, 0}, aw = {smem + warp * 128 + 64, 0};
+    int my_bound = 0;
+    unsigned long long my_h = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         wbase < P.n; wbase += stride) {
+        const long long i = wbase + lane_id();
+        const bool valid = i < P.n;
+        int k = 0;
+        if (valid) {
+            const int v = (int)i;
+            const int beg = __ldg(P.r_ptr + v);
+            const int d = __ldg(P.r_ptr + v + 1) - beg;
+            P.deg[v] = d;
+            P.col[v] = 0;
+            P.lose[v] = 0;
+            k = d + P.self;
+            long long b = 0;
+            for (int j = 0; j < k; ++j) b += net_size(P, vertex_net(P, v, beg, j)) - 1;
+            my_bound = max(my_bound, (int)min(b, (long long)INT32_MAX - 1));
+            my_h += (unsigned long long)k;
+        }
+        wa_push(at, valid && k <= kThreadNets, (int)i, P.wt[1], &st->nt[1]);
+        wa_push(aw, valid && k > kThreadNets, (int)i, P.ww[1], &st->nw[1]);
+    }
+    wa_flush(at, P.wt[1], &st->nt[1]);
+    wa_flush(aw, P.ww[1], &st->nw[1]);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < P.n_nets; q += stride)
+        P.net_flag[q] = 0;
+    my_bound = warp_max(my_bound);
+    my_h = warp_sum(my_h);
+    if (lane_id() == 0) {
+        atomicMax(&st->bound, my_bound);
+        if (my_h) atomicAdd(&st->h_first, my_h);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->round = 1;
+        st->t0 = global_ns();
+        if (P.trace_cap > 0) {
+            P.trace_w[0] = P.n;
+            P.trace_s[0] = __ldg(P.r_ptr + P.n);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// assign: OR the nets' masks window by window, take the first free color
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mark_net(const Problem& P, int q, int r) {
+    if (P.net_flag[q] != r) P.net_flag[q] = r;
+}
+
+__global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
+                           int use_cond) {
+    const Problem& P = *Pp;
+    State* st = P.st;
+    // The loop continues only if this round's commit says so.
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    const int r = *(volatile int*)&st->round;
+    const int cp = r & 1;
+    const int nT = st->nt[cp], nW = st->nw[cp];
+    const unsigned long long* mk = P.mask;
+    const long long nn = P.n_nets;
+    // thread tier
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += stride) {
+        const int v = P.wt[cp][i];
+        const int beg = __ldg(P.r_ptr + v);
+        const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
+        int t = 0;
+        for (int w = 0; w < P.windows && t == 0; ++w) {
+            unsigned long long f = 0ull;
+            for (int j = 0; j < k; ++j) f |= mk[w * nn + vertex_net(P, v, beg, j)];
+            if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
+        }
+        if (t == 0) {
+            atomicExch(&st->status, ST_OVERFLOW);
+            t = 64 * P.windows;
+        }
+        P.col[v] = -t;
+        for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
+    }
+    // warp tier
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nW; i += gridDim.x * wpb) {
+        const int v = P.ww[cp][i];
+        const int beg = __ldg(P.r_ptr + v);
+        const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
+        int t = 0;
+        for (int w = 0; w < P.windows && t == 0; ++w) {
+            unsigned long long f = 0ull;
+            for (int j = lane; j < k; j += 32) f |= mk[w * nn + vertex_net(P, v, beg, j)];
+            const unsigned lo = __reduce_or_sync(kFullMask, (unsigned)f);
+            const unsigned hi = __reduce_or_sync(kFullMask, (unsigned)(f >> 32));
+            f = ((unsigned long long)hi << 32) | lo;
+            if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
+        }
+        if (t == 0) {
+            if (lane == 0) atomicExch(&st->status, ST_OVERFLOW);
+            t = 64 * P.windows;
+        }
+        if (lane == 0) P.col[v] = -t;
+        for (int j = lane; j < k; j += 32) mark_net(P, vertex_net(P, v, beg, j), r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// detect: per active net, flag members that share a color with a member of
+// higher priority.  Members holding a committed (positive) color never
+// match: first fit excluded every committed color of v's nets.
+// ---------------------------------------------------------------------------
+__global__ void net_detect(const Problem* __restrict__ Pp) {
+    const Problem& P = *Pp;
+    const int r = *(volatile int*)&P.st->round;
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const unsigned long long seed = P.seed;
+    const bool use_deg = P.use_deg != 0;
+    const int nn = P.n_nets;
+    // each warp reads 32 net flags at a time and handles the active ones
+    for (long long b0 = ((long long)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; b0 < nn;
+         b0 += (long long)gridDim.x * wpb * 32) {
+      unsigned act = __ballot_sync(kFullMask, b0 + lane < nn && P.net_flag[b0 + lane] == r);
+      while (act) {
+        const int q = (int)b0 + __ffs(act) - 1;
+        act &= act - 1;
+        const int m = net_size(P, q);
+        if (m <= 32) {
+            int x = -1, c = 0, d = 0;
+            if (lane < m) {
+                x = net_member(P, q, lane);
+                const int cx = P.col[x];
+                c = cx < 0 ? -cx : 0;   // only uncolored members can conflict
+                if (c) d = __ldg(P.deg + x);
+            }
+            // lanes holding the same uncolored color as some other lane
+            const unsigned grp = __match_any_sync(kFullMask, c) & ~(1u << lane);
+            // each such lane broadcasts (id, color, degree); every uncolored
+            // lane of the same color checks whether the source has priority
+            bool lose = false;
+            const uint64_t hx = c ? prio_hash(seed, (uint32_t)x) : 0ull;
+            unsigned any = __ballot_sync(kFullMask, c != 0 && grp != 0);
+            while (any) {
+                const int src = __ffs(any) - 1;
+                any &= any - 1;
+                const int xs = __shfl_sync(kFullMask, x, src);
+                const int cs = __shfl_sync(kFullMask, c, src);
+                const int ds = __shfl_sync(kFullMask, d, src);
+                if (c && src != lane && cs == c && xs != x && higher(ds, xs, d, hx, x, seed, use_deg))
+                    lose = true;
+            }
+            if (lose) P.lose[x] = 1;
+        } else {
+            // large net: every uncolored member against every other member
+            for (int i0 = 0; i0 < m; i0 += 32) {
+                int x = -1, c = 0, d = 0;
+                if (i0 + lane < m) {
+                    x = net_member(P, q, i0 + lane);
+                    const int cx = P.col[x];
+                    c = cx < 0 ? -cx : 0;
+                    if (c) d = __ldg(P.deg + x);
+                }
+                const uint64_t hx = c ? prio_hash(seed, (uint32_t)x) : 0ull;
+                bool lose = false;
+                for (int j0 = 0; j0 < m; j0 += 32) {
+                    int y = -1, cy = 0, dy = 0;
+                    if (j0 + lane < m) {
+                        y = net_member(P, q, j0 + lane);
+                        const int c2 = P.col[y];
+                        cy = c2 < 0 ? -c2 : 0;
+                        if (cy) dy = __ldg(P.deg + y);
+                    }
+                    unsigned cand = __ballot_sync(kFullMask, cy != 0);
+                    while (cand) {
+                        const int src = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        const int ys = __shfl_sync(kFullMask, y, src);
+                        const int cs = __shfl_sync(kFullMask, cy, src);
+                        const int ds = __shfl_sync(kFullMask, dy, src);
+                        if (c && cs == c && ys != x && higher(ds, ys, d, hx, x, seed, use_deg))
+                            lose = true;
+                    }
+                }
+                if (lose) P.lose[x] = 1;
+            }
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// commit + compact + mask update (+ round control in the last block)
+// ---------------------------------------------------------------------------
+__device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, int use_cond) {
+    State* st = P.st;
+    const int r = st->round;
+    const int cp = r & 1, np = cp ^ 1;
+    const long long cur = (long long)st->nt[cp] + st->nw[cp];
+    const long long nxt = (long long)*(volatile int*)&st->nt[np] + *(volatile int*)&st->nw[np];
+    if (r < P.trace_cap) {
+        P.trace_w[r] = nxt;
+        P.trace_s[r] = (long long)*(volatile unsigned long long*)&st->s_next;
+        P.trace_h[r] = (long long)*(volatile unsigned long long*)&st->h_next;
+    }
+    if (r == 1 && P.trace_cap > 0) P.trace_h[0] = (long long)st->h_first;
+    int done = 0;
+    int status = *(volatile int*)&st->status;
+    if (status != ST_OK) {
+        done = 1;
+    } else if (nxt == 0) {
+        done = 1;
+    } else if (nxt >= cur) {
+        done = 1;
+        status = ST_NO_PROGRESS;
+    } else if (r >= P.max_rounds) {
+        done = 1;
+        status = ST_MAX_ROUNDS;
+    } else if (global_ns() - st->t0 > P.timeout_ns) {
+        done = 1;
+        status = ST_TIMEOUT;
+    }
+    if (!done) {
+        st->nt[cp] = st->nw[cp] = 0;
+        st->round = r + 1;
+        st->s_next = 0ull;
+        st->h_next = 0ull;
+    }
+    st->status = status;
+    st->done = done;
+    st->blocks_done = 0u;
+    __threadfence();
+    if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
+__global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
+                           int use_cond) {
+    extern __shared__ int smem[];
+    const Problem& P = *Pp;
+    State* st = P.st;
+    const int r = *(volatile int*)&st->round;
+    const int cp = r & 1, np = cp ^ 1;
+    const int nT = st->nt[cp], nW = st->nw[cp];
+    const long long total = (long long)nT + nW;
+    const long long nn = P.n_nets;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    WarpAppend at = {smem + warp * 128, 0}, aw = {smem + warp * 128 + 64, 0};
+    int my_max = 0;
+    unsigned long long my_s = 0ull, my_h = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < total;
+         wbase += stride) {
+        const long long i = wbase + lane;
+        bool lost = false, thread_tier = false;
+        int v = -1;
+        if (i < total) {
+            thread_tier = i < nT;
+            v = thread_tier ? P.wt[cp][i] : P.ww[cp][i - nT];
+            const int beg = __ldg(P.r_ptr + v);
+            const int d = __ldg(P.r_ptr + v + 1) - beg;
+            const int k = d + P.self;
+            if (P.lose[v]) {
+                P.lose[v] = 0;
+                lost = true;
+                my_s += (unsigned long long)d;
+                my_h += (unsigned long long)k;
+            } else {
+                const int t = -P.col[v];
+                P.col[v] = t;
+                my_max = max(my_max, t);
+                const int w = (t - 1) >> 6;
+                const unsigned long long bit = 1ull << ((t - 1) & 63);
+                for (int j = 0; j < k; ++j)
+                    atomicOr(P.mask + w * nn + vertex_net(P, v, beg, j), bit);
+            }
+        }
+        wa_push(at, lost && thread_tier, v, P.wt[np], &st->nt[np]);
+        wa_push(aw, lost && !thread_tier, v, P.ww[np], &st->nw[np]);
+    }
+    wa_flush(at, P.wt[np], &st->nt[np]);
+    wa_flush(aw, P.ww[np], &st->nw[np]);
+    my_max = warp_max(my_max);
+    my_s = warp_sum(my_s);
+    my_h = warp_sum(my_h);
+    if (lane == 0) {
+        if (my_max > 0) atomicMax(&st->max_color, my_max);
+        if (my_s > 0) atomicAdd(&st->s_next, my_s);
+        if (my_h > 0) atomicAdd(&st->h_next, my_h);
+    }
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        round_control(P, h, use_cond);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Context {
+    std::mutex mu;
+    DeviceInfo dev;
+    DevBuf deg, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col;
+    HostBuf h_problem, h_state, h_misc;
+    int trace_cap = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+    int g_grid = 0, g_block = 0;
+
+    void destroy_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        g_grid = 0;
+    }
+    void release() {
+        destroy_graph();
+        for (DevBuf* b : {&deg, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
+                          &stage_col, &stage[0], &stage[1], &stage[2], &stage[3]})
+            b->release();
+        for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
+        trace_cap = 0;
+    }
+};
+
+static std::mutex g_ctx_mu;
+static std::unordered_map<int, std::unique_ptr<Context>>& contexts() {
+    static std::unordered_map<int, std::unique_ptr<Context>> m;
+    return m;
+}
+
+static Context* get_context(int device) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    auto& m = contexts();
+    auto it = m.find(device);
+    if (it != m.end()) return it->second.get();
+    static bool hooked = false;
+    if (!hooked) {
+        hooked = true;
+        release_hooks().push_back([] {
+            std::lock_guard<std::mutex> lk2(g_ctx_mu);
+            int cur = 0;
+            cudaGetDevice(&cur);
+            auto f = contexts().find(cur);
+            if (f != contexts().end()) {
+                std::lock_guard<std::mutex> lk3(f->second->mu);
+                f->second->release();
+            }
+        });
+    }
+    auto c = std::make_unique<Context>();
+    Context* p = c.get();
+    m.emplace(device, std::move(c));
+    return p;
+}
+
+struct Geometry {
+    int grid, block;
+    size_t smem;
+};
+
+static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
+    g->block = o.block;
+    g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
+    int per_sm = o.grid_per_sm;
+    if (per_sm == 0) {
+        int a = 0, b = 0;
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, net_detect, o.block, 0));
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, net_commit, o.block, g->smem));
+        per_sm = std::max(1, std::min(a, b));
+    }
+    g->grid = cx.dev.num_sms * per_sm;
+    return PGC_OK;
+}
+
+static cudaKernelNodeParams knode(void* func, const Geometry& g, size_t smem, void** args) {
+    cudaKernelNodeParams k = {};
+    k.func = func;
+    k.gridDim = dim3(g.grid);
+    k.blockDim = dim3(g.block);
+    k.sharedMemBytes = (unsigned)smem;
+    k.kernelParams = args;
+    return k;
+}
+
+// {assign, detect, commit} inside a WHILE node that starts with condition 1.
+static pgc_status build_graph(Context& cx, const Geometry& g) {
+    cx.destroy_graph();
+    Problem* dP = cx.problem.as<Problem>();
+    PGC_CUDA(cudaGraphCreate(&cx.graph, 0));
+    PGC_CUDA(cudaGraphConditionalHandleCreate(&cx.handle, cx.graph, 1u, cudaGraphCondAssignDefault));
+    int use_cond = 1;
+    cudaGraphConditionalHandle hnd = cx.handle;
+    void* p_args[] = {&dP};
+    void* c_args[] = {&dP, &hnd, &use_cond};
+    cudaGraphNode_t n_loop;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cx.handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    PGC_CUDA(cudaGraphAddNode(&n_loop, cx.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaKernelNodeParams k_asg = knode((void*)net_assign, g, 0, c_args);
+    cudaKernelNodeParams k_det = knode((void*)net_detect, g, 0, p_args);
+    cudaKernelNodeParams k_com = knode((void*)net_commit, g, g.smem, c_args);
+    cudaGraphNode_t b_asg, b_det, b_com;
+    PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
+    PGC_CUDA(cudaGraphAddKernelNode(&b_det, body, &b_asg, 1, &k_det));
+    PGC_CUDA(cudaGraphAddKernelNode(&b_com, body, &b_det, 1, &k_com));
+    PGC_CUDA(cudaGraphInstantiate(&cx.exec, cx.graph, 0));
+    cx.g_grid = g.grid;
+    cx.g_block = g.block;
+    return PGC_OK;
+}
+
+struct Input {
+    int n, n_nets, self;
+    const int *m_ptr, *m_idx, *r_ptr, *r_idx;
+    int* col;
+};
+
+static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o,
+                      cudaStream_t stream, int* rounds, int* num_colors) {
+    const int n = in.n;
+    if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
+    if (pgc_status s = cx.lose.ensure((size_t)n * 4)) return s;
+    if (pgc_status s = cx.flag.ensure((size_t)std::max(in.n_nets, 1) * 4)) return s;
+    if (pgc_status s = cx.wt.ensure((size_t)n * 4 * 2)) return s;
+    if (pgc_status s = cx.ww.ensure((size_t)n * 4 * 2)) return s;
+    if (pgc_status s = cx.state.ensure(sizeof(State))) return s;
+    if (pgc_status s = cx.problem.ensure(sizeof(Problem))) return s;
+    if (pgc_status s = cx.h_problem.ensure(sizeof(Problem))) return s;
+    if (pgc_status s = cx.h_state.ensure(sizeof(State))) return s;
+    const int want_trace = o.profile && o.profile->trace_cap > 0 ? o.profile->trace_cap : 0;
+    const int tcap = std::max(want_trace, 1);
+    if (cx.trace_cap < tcap) {
+        if (pgc_status s = cx.trace.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
+        if (pgc_status s = cx.h_misc.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
+        cx.trace_cap = tcap;
+    }
+    Geometry g;
+    if (pgc_status s = geometry(cx, o, &g)) return s;
+
+    Problem* hp = cx.h_problem.as<Problem>();
+    std::memset(hp, 0, sizeof(Problem));
+    hp->m_ptr = in.m_ptr;
+    hp->m_idx = in.m_idx;
+    hp->r_ptr = in.r_ptr;
+    hp->r_idx = in.r_idx;
+    hp->col = in.col;
+    hp->deg = cx.deg.as<int>();
+    hp->lose = cx.lose.as<int>();
+    hp->net_flag = cx.flag.as<int>();
+    for (int p = 0; p < 2; ++p) {
+        hp->wt[p] = cx.wt.as<int>() + (size_t)p * n;
+        hp->ww[p] = cx.ww.as<int>() + (size_t)p * n;
+    }
+    hp->trace_w = cx.trace.as<long long>();
+    hp->trace_s = hp->trace_w + tcap;
+    hp->trace_h = hp->trace_s + tcap;
+    hp->trace_cap = want_trace;
+    hp->st = cx.state.as<State>();
+    hp->seed = seed;
+    hp->timeout_ns = (unsigned long long)o.timeout_ms * 1000000ull;
+    hp->n = n;
+    hp->n_nets = in.n_nets;
+    hp->self = in.self;
+    hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
+    hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
+    hp->windows = 1;
+    Problem* dP = cx.problem.as<Problem>();
+    State* hs = cx.h_state.as<State>();
+
+    // setup, then the color bound decides how many 64-color mask windows
+    PGC_CUDA(cudaMemcpyAsync(dP, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
+    PGC_CUDA(cudaMemsetAsync(cx.state.ptr, 0, sizeof(State), stream));
+    KernelTimer kt;
+    kt.prof = (o.flags & PGC_HOST_LOOP) ? o.profile : nullptr;
+    kt.stream = stream;
+    if (pgc_status s = kt.begin(0, "net_init")) return s;
+    net_init<<<g.grid, g.block, g.smem, stream>>>(dP);
+    PGC_CUDA(cudaGetLastError());
+    if (pgc_status s = kt.end()) return s;
+    PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
+    PGC_CUDA(cudaStreamSynchronize(stream));
+    const long long need = (long long)hs->bound + 1;   // a first-fit color is <= |S(v)| + 1
+    const int windows = (int)std::min<long long>(kMaxWindows, (need + 63) / 64);
+    hp->windows = std::max(1, windows);
+    const size_t mask_bytes = (size_t)hp->windows * (size_t)std::max(in.n_nets, 1) * 8;
+    if (pgc_status s = cx.mask.ensure(mask_bytes)) return s;
+    hp->mask = cx.mask.as<unsigned long long>();
+    PGC_CUDA(cudaMemcpyAsync(dP, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
+    PGC_CUDA(cudaMemsetAsync(cx.mask.ptr, 0, mask_bytes, stream));
+
+    if (!(o.flags & PGC_HOST_LOOP)) {
+        if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block) {
+            if (pgc_status s = build_graph(cx, g)) return s;
+        }
+        PGC_CUDA(cudaGraphLaunch(cx.exec, stream));
+    } else {
+        const cudaGraphConditionalHandle none = 0;
+        for (int round = 1;; ++round) {
+            if (pgc_status s = kt.begin(1, "net_assign")) return s;
+            net_assign<<<g.grid, g.block, 0, stream>>>(dP, none, 0);
+            PGC_CUDA(cudaGetLastError());
+            if (pgc_status s = kt.end()) return s;
+            if (pgc_status s = kt.begin(2, "net_detect")) return s;
+            net_detect<<<g.grid, g.block, 0, stream>>>(dP);
+            PGC_CUDA(cudaGetLastError());
+            if (pgc_status s = kt.end()) return s;
+            if (pgc_status s = kt.begin(3, "net_commit")) return s;
+            net_commit<<<g.grid, g.block, g.smem, stream>>>(dP, none, 0);
+            PGC_CUDA(cudaGetLastError());
+            if (pgc_status s = kt.end()) return s;
+            PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
+            PGC_CUDA(cudaStreamSynchronize(stream));
+            if (hs->done) break;
+            if (round > hp->max_rounds + 1)
+                return fail(PGC_ERR_CUDA, "device round control did not finish the loop");
+        }
+    }
+    kt.destroy();
+    PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
+    if (want_trace) {
+        PGC_CUDA(cudaMemcpyAsync(cx.h_misc.ptr, cx.trace.ptr, (size_t)tcap * 3 * sizeof(long long),
+                                 cudaMemcpyDeviceToHost, stream));
+    }
+    PGC_CUDA(cudaStreamSynchronize(stream));
+    if (want_trace) {
+        const long long* tw = cx.h_misc.as<long long>();
+        const long long* ts = tw + tcap;
+        const long long* th = ts + tcap;
+        const int nr = std::min(hs->round, want_trace);
+        for (int i = 0; i < want_trace; ++i) {
+            if (o.profile->trace_w) o.profile->trace_w[i] = i < nr ? tw[i] : 0;
+            if (o.profile->trace_s) o.profile->trace_s[i] = i < nr ? ts[i] : 0;
+            if (o.profile->trace_h) o.profile->trace_h[i] = i < nr ? th[i] : 0;
+        }
+    }
+    *rounds = hs->round;
+    *num_colors = hs->max_color;
+    switch (hs->status) {
+        case ST_OK: return PGC_OK;
+        case ST_NO_PROGRESS:
+            return fail(PGC_ERR_NO_CONVERGE, "a round committed no vertex (inconsistent input?)");
+        case ST_MAX_ROUNDS: return fail(PGC_ERR_NO_CONVERGE, "max_rounds reached");
+        case ST_TIMEOUT: return fail(PGC_ERR_TIMEOUT, "device round loop exceeded timeout_ms");
+        case ST_OVERFLOW:
+            return fail(PGC_ERR_NO_CONVERGE, "a color above 4096 was needed (mask capacity)");
+        default: return fail(PGC_ERR_CUDA, "unexpected device status");
+    }
+}
+
+// Reads a[idx] whether a is host or device memory.
+static pgc_status read_int(const int* a, bool host, long long idx, int* out, Context& cx,
+                           cudaStream_t stream) {
+    if (host) {
+        *out = a[idx];
+        return PGC_OK;
+    }
+    if (pgc_status s = cx.h_state.ensure(sizeof(State))) return s;
+    int* hb = cx.h_state.as<int>();
+    PGC_CUDA(cudaMemcpyAsync(hb, a + idx, 4, cudaMemcpyDeviceToHost, stream));
+    PGC_CUDA(cudaStreamSynchronize(stream));
+    *out = *hb;
+    return PGC_OK;
+}
+
+// Stages a host array of count ints into slot; returns the device pointer.
+static pgc_status stage(Context& cx, int slot, const int* a, long long count, cudaStream_t stream,
+                        const int** out) {
+    if (!is_host_pointer(a)) {
+        *out = a;
+        return PGC_OK;
+    }
+    if (pgc_status s = cx.stage[slot].ensure((size_t)std::max<long long>(count, 1) * 4)) return s;
+    if (count > 0)
+        PGC_CUDA(cudaMemcpyAsync(cx.stage[slot].ptr, a, (size_t)count * 4, cudaMemcpyHostToDevice,
+                                 stream));
+    *out = cx.stage[slot].as<int>();
+    return PGC_OK;
+}
+
+static pgc_status color(int kind, int32_t n_rows, int32_t n_cols, const int32_t* row_ptr,
+                        const int32_t* col_idx, const int32_t* col_ptr, const int32_t* row_idx,
+                        uint64_t seed, int32_t* colors, int32_t* rounds, int32_t* num_colors,
+                        const pgc_opts* opts, void* stream_v) {
+    if (!rounds || !num_colors) return fail(PGC_ERR_INVALID_ARG, "rounds/num_colors must be non-NULL");
+    if (n_rows < 0 || n_cols < 0) return fail(PGC_ERR_INVALID_ARG, "negative size");
+    Opts o;
+    if (pgc_status s = read_opts(opts, &o)) return s;
+    *rounds = 0;
+    *num_colors = 0;
+    const int n = kind == 2 ? n_rows : n_cols;
+    if (n == 0) return PGC_OK;
+    if (!row_ptr || !colors || (kind == 3 && !col_ptr))
+        return fail(PGC_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    DeviceInfo dev;
+    if (pgc_status s = current_device(&dev)) return s;
+    Context* cx = get_context(dev.device);
+    std::lock_guard<std::mutex> lk(cx->mu);
+    cx->dev = dev;
+
+    int nnz = 0, nnz_c = 0;
+    if (pgc_status s = read_int(row_ptr, is_host_pointer(row_ptr), n_rows, &nnz, *cx, stream))
+        return s;
+    if (nnz < 0) return fail(PGC_ERR_INVALID_ARG, "row_ptr[n] < 0");
+    if (nnz > 0 && !col_idx) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx");
+    if (kind == 3) {
+        if (pgc_status s = read_int(col_ptr, is_host_pointer(col_ptr), n_cols, &nnz_c, *cx, stream))
+            return s;
+        if (nnz_c != nnz) return fail(PGC_ERR_INVALID_ARG, "CSR and CSC have different nnz");
+        if (nnz > 0 && !row_idx) return fail(PGC_ERR_INVALID_ARG, "NULL row_idx");
+    }
+    Input in;
+    in.self = kind == 2 ? 1 : 0;
+    in.n = n;
+    in.n_nets = n_rows;
+    if (pgc_status s = stage(*cx, 0, row_ptr, (long long)n_rows + 1, stream, &in.m_ptr)) return s;
+    if (nnz > 0) {
+        if (pgc_status s = stage(*cx, 1, col_idx, nnz, stream, &in.m_idx)) return s;
+    } else {
+        in.m_idx = col_idx;
+    }
+    if (kind == 2) {
+        in.r_ptr = in.m_ptr;
+        in.r_idx = in.m_idx;
+    } else {
+        if (pgc_status s = stage(*cx, 2, col_ptr, (long long)n_cols + 1, stream, &in.r_ptr))
+            return s;
+        if (nnz > 0) {
+            if (pgc_status s = stage(*cx, 3, row_idx, nnz, stream, &in.r_idx)) return s;
+        } else {
+            in.r_idx = row_idx;
+        }
+    }
+    const bool host_col = is_host_pointer(colors);
+    in.col = colors;
+    if (host_col) {
+        if (pgc_status s = cx->stage_col.ensure((size_t)n * 4)) return s;
+        in.col = cx->stage_col.as<int>();
+    }
+    pgc_status s = run(*cx, in, seed, o, stream, rounds, num_colors);
+    if (s != PGC_OK) return s;
+    if (host_col) {
+        PGC_CUDA(cudaMemcpyAsync(colors, in.col, (size_t)n * 4, cudaMemcpyDeviceToHost, stream));
+        PGC_CUDA(cudaStreamSynchronize(stream));
+    }
+    return PGC_OK;
+}
+
+}  // namespace net
+}  // namespace pgc
+
+extern "C" pgc_status pgc_color_d2(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                   uint64_t seed, int32_t* colors, int32_t* rounds,
+                                   int32_t* num_colors, const pgc_opts* opts, void* stream) {
+    try {
+        return pgc::net::color(2, n, n, row_ptr, col_idx, nullptr, nullptr, seed, colors, rounds,
+                               num_colors, opts, stream);
+    } catch (const std::exception& e) {
+        return pgc::fail(PGC_ERR_CUDA, e.what());
+    } catch (...) {
+        return pgc::fail(PGC_ERR_CUDA, "unknown exception");
+    }
+}
+
+extern "C" pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr,
+                                    const int32_t* col_idx, const int32_t* col_ptr,
+                                    const int32_t* row_idx, uint64_t seed, int32_t* colors,
+                                    int32_t* rounds, int32_t* num_colors, const pgc_opts* opts,
+                                    void* stream) {
+    try {
+        return pgc::net::color(3, n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed, colors,
+                               rounds, num_colors, opts, stream);
+    } catch (const std::exception& e) {
+        return pgc::fail(PGC_ERR_CUDA, e.what());
+    } catch (...) {
+        return pgc::fail(PGC_ERR_CUDA, "unknown exception");
+    }
+}

@@ -1,0 +1,28 @@
+"""Inputs and oracle runs for the full-size parity tests (run in spawned
+worker processes: no CUDA here)."""
+import oracle
+from paper_2107_00075_gb300 import inputs as gen
+
+CASES = ("rmat24_d1", "stencil128_d2", "bip_pd2")
+
+
+def make_input(kind):
+    if kind == "rmat24_d1":
+        return gen.rmat(24, 16, seed=1)
+    if kind == "stencil128_d2":
+        return gen.stencil3d(128, 128, 128, points=27)
+    if kind == "bip_pd2":
+        return gen.bipartite(1 << 22, 1 << 20, lam=7.0, seed=1)
+    raise ValueError(kind)
+
+
+def oracle_job(kind):
+    x = make_input(kind)
+    if kind == "rmat24_d1":
+        r = oracle.color_d1(x.row_ptr, x.col_idx, seed=1)
+    elif kind == "stencil128_d2":
+        r = oracle.color_d2(x.row_ptr, x.col_idx, seed=1)
+    else:
+        r = oracle.color_pd2(x.n_rows, x.n_cols, x.row_ptr, x.col_idx, x.col_ptr, x.row_idx,
+                             seed=1)
+    return r.colors, r.rounds, r.num_colors, r.trace_w, r.trace_s

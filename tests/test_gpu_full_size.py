@@ -1,23 +1,46 @@
-"""Parity at the benchmark's full size, in the launch configuration bench.py
-times: distance-1 coloring of R-MAT scale 24 (16.8M vertices, ~521M CSR
-entries) compared with the oracle element by element, plus the properness
-and Grundy checks that hold at any size."""
+"""Parity at full size, in the launch configuration bench.py times.
+
+  * D1 on R-MAT scale 24 (16.8M vertices, ~521M CSR entries);
+  * D2 on the 27-point stencil 128^3 (2.1M vertices, 53.6M entries);
+  * PD2 on the 4M x 1M random Jacobian pattern (rows 1 + Poisson(7)).
+
+The colors are compared with the oracle element by element.  The three
+oracle runs take minutes of single-threaded CPU time, so they run in
+parallel in spawned worker processes while the GPU side runs here."""
+import multiprocessing as mp
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 import pytest
 
 import oracle
-from paper_2107_00075_gb300 import inputs as gen
+from tests import _full_size_jobs as jobs
 
 pytestmark = pytest.mark.gpu
 
 
-def test_rmat24_d1_bit_exact():
+@pytest.fixture(scope="module")
+def oracle_futures():
+    ex = ProcessPoolExecutor(max_workers=3, mp_context=mp.get_context("spawn"))
+    futs = {k: ex.submit(jobs.oracle_job, k) for k in jobs.CASES}
+    yield futs
+    ex.shutdown(wait=False, cancel_futures=True)
+
+
+def _compare(got, rounds, ncol, prof, want):
+    w_colors, w_rounds, w_ncol, w_tw, w_ts = want
+    assert rounds == w_rounds and ncol == w_ncol
+    diff = np.count_nonzero(got != w_colors)
+    assert diff == 0, f"{diff} of {len(got)} colors differ"
+    assert np.array_equal(prof.trace_w, w_tw)
+    assert np.array_equal(prof.trace_s, w_ts)
+
+
+def test_rmat24_d1_bit_exact(oracle_futures):
     import torch
     import paper_2107_00075_gb300 as pgc
-    g = gen.rmat(24, 16, seed=1)
-    assert g.n == 1 << 24
+    g = jobs.make_input("rmat24_d1")
     rp = torch.from_numpy(g.row_ptr).cuda()
     ci = torch.from_numpy(g.col_idx).cuda()
     prof = pgc.Profile(trace_cap=1 << 16)
@@ -25,12 +48,35 @@ def test_rmat24_d1_bit_exact():
     colors = r.colors.cpu().numpy()
     del rp, ci
     t0 = time.time()
-    want = oracle.color_d1(g.row_ptr, g.col_idx, seed=1)
-    print(f"oracle on R-MAT 24: {time.time() - t0:.1f} s, {want.rounds} rounds")
-    assert r.rounds == want.rounds and r.num_colors == want.num_colors
-    diff = np.count_nonzero(colors != want.colors)
-    assert diff == 0, f"{diff} of {g.n} colors differ"
-    assert np.array_equal(prof.trace_w, want.trace_w)
-    assert np.array_equal(prof.trace_s, want.trace_s)
+    want = oracle_futures["rmat24_d1"].result()
+    print(f"waited {time.time() - t0:.1f} s for the oracle")
+    _compare(colors, r.rounds, r.num_colors, prof, want)
     assert oracle.count_improper(oracle.D1, g.row_ptr, g.col_idx, colors) == 0
     assert oracle.count_non_grundy(oracle.D1, g.row_ptr, g.col_idx, colors) == 0
+
+
+def test_stencil128_d2_bit_exact(oracle_futures):
+    import torch
+    import paper_2107_00075_gb300 as pgc
+    g = jobs.make_input("stencil128_d2")
+    assert g.n == 128 ** 3 and g.nnz == 53_645_816
+    prof = pgc.Profile(trace_cap=1 << 16)
+    r = pgc.pgc_color_d2(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(),
+                         seed=1, profile=prof)
+    colors = r.colors.cpu().numpy()
+    _compare(colors, r.rounds, r.num_colors, prof, oracle_futures["stencil128_d2"].result())
+    assert r.num_colors >= 27
+
+
+def test_bipartite_pd2_bit_exact(oracle_futures):
+    import torch
+    import paper_2107_00075_gb300 as pgc
+    b = jobs.make_input("bip_pd2")
+    assert b.n_rows == 1 << 22 and b.n_cols == 1 << 20
+    prof = pgc.Profile(trace_cap=1 << 16)
+    t = lambda a: torch.from_numpy(a).cuda()
+    r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, t(b.row_ptr), t(b.col_idx), t(b.col_ptr),
+                          t(b.row_idx), seed=1, profile=prof)
+    colors = r.colors.cpu().numpy()
+    _compare(colors, r.rounds, r.num_colors, prof, oracle_futures["bip_pd2"].result())
+    assert r.num_colors >= np.diff(b.row_ptr).max()
