@@ -72,6 +72,11 @@ typedef enum {
 #define PGC_HOST_LOOP      0x4u  /* drive rounds from the host (one sync per round)
                                     instead of the device-side graph loop; enables
                                     per-kernel timing in pgc_profile */
+#define PGC_AUTOTUNE       0x8u  /* pgc_color_d1_batch: time a few launch
+                                    configurations on the first batch of a size
+                                    class, reuse the fastest (in memory, and in
+                                    the file named by $PGC_TUNE_FILE if set);
+                                    colors never depend on the choice */
 
 /* Per-kernel timing and per-round trace, filled when non-NULL in pgc_opts. */
 #define PGC_MAX_KERNELS 8
@@ -163,6 +168,29 @@ pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_t *row_ptr,
                          const int32_t *row_idx, uint64_t seed, int32_t *colors,
                          int32_t *rounds, int32_t *num_colors, const pgc_opts *opts,
                          void *stream);
+
+/*
+ * Batched distance-1 coloring of G independent graphs in one launch (the
+ * batched form of Sec. 3.2; the paper has no batched API).  Graph g has
+ * n_g = vtx_off[g+1] - vtx_off[g] vertices and m_g = nnz_off[g+1] - nnz_off[g]
+ * adjacency entries; ids, degrees and the priority hash are graph-local, so
+ * each graph's colors, rounds and color count equal those of pgc_color_d1 on
+ * that graph alone with the same seed and flags.
+ *   vtx_off, nnz_off int64[G+1], prefix offsets starting at 0
+ *   row_ptr int32[N + G]: graph g's local row_ptr (n_g + 1 entries, from 0
+ *           to m_g) at row_ptr[vtx_off[g] + g ...]   (N = vtx_off[G] < 2^31)
+ *   col_idx int32[nnz_off[G]]: graph g's local ids in [0, n_g) at
+ *           col_idx[nnz_off[g] ...]; each graph symmetric
+ *   colors  int32[N] output (graph g at colors[vtx_off[g] ...])
+ *   rounds_per_g, ncolors_per_g  int32[G] outputs (0 for empty graphs)
+ *   rounds  host int32*, nullable: rounds of the whole launch (the maximum
+ *           over the graphs)
+ * Any array may be host or device memory.  PGC_AUTOTUNE applies here.
+ */
+pgc_status pgc_color_d1_batch(int32_t G, const int64_t *vtx_off, const int64_t *nnz_off,
+                              const int32_t *row_ptr, const int32_t *col_idx, uint64_t seed,
+                              int32_t *colors, int32_t *rounds_per_g, int32_t *ncolors_per_g,
+                              int32_t *rounds, const pgc_opts *opts, void *stream);
 
 /* Message for the last error on this thread ("" if none). */
 const char *pgc_last_error(void);

@@ -20,6 +20,7 @@ PGC_OK = 0
 PGC_NO_DEGREE_RULE = 0x1
 PGC_VALIDATE = 0x2
 PGC_HOST_LOOP = 0x4
+PGC_AUTOTUNE = 0x8
 PGC_MAX_KERNELS = 8
 
 STATUS_NAMES = {0: "PGC_OK", 1: "PGC_ERR_INVALID_ARG", 2: "PGC_ERR_CUDA", 3: "PGC_ERR_OOM",
@@ -88,6 +89,9 @@ def lib():
         L.pgc_color_pd2.argtypes = [i32, i32, p, p, p, p, u64, p, ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_pd2.restype = ctypes.c_int
+        L.pgc_color_d1_batch.argtypes = [i32, p, p, p, p, u64, p, p, p, ctypes.POINTER(i32),
+                                         ctypes.POINTER(PgcOptsC), p]
+        L.pgc_color_d1_batch.restype = ctypes.c_int
         L.pgc_last_error.restype = ctypes.c_char_p
         L.pgc_status_string.argtypes = [ctypes.c_int]
         L.pgc_status_string.restype = ctypes.c_char_p
@@ -271,6 +275,65 @@ def _color_sym(fname, row_ptr, col_idx, seed, colors, flags, max_rounds, mid_deg
     _check(st)
     _finish_profile(profile, keep, rounds.value)
     return ColorResult(colors, rounds.value, ncol.value)
+
+
+@dataclass
+class BatchResult:
+    colors: object
+    rounds_per_graph: object
+    colors_per_graph: object
+    rounds: int
+
+
+class _Arr64:
+    def __init__(self, a, name):
+        try:
+            import torch
+        except ImportError:  # pragma: no cover
+            torch = None
+        self.device = None
+        if torch is not None and isinstance(a, torch.Tensor):
+            if a.dtype != torch.int64 or not a.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous int64 tensor")
+            self.obj, self.ptr, self.n = a, a.data_ptr(), a.numel()
+            self.device = a.device if a.is_cuda else None
+        else:
+            arr = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+            self.obj, self.ptr, self.n = arr, arr.ctypes.data, arr.size
+
+
+def pgc_color_d1_batch(vtx_off, nnz_off, row_ptr, col_idx, seed: int = 1, colors=None,
+                       rounds_per_graph=None, colors_per_graph=None, *, flags: int = 0,
+                       max_rounds: int = 0, mid_degree: int = 0, hub_degree: int = 0,
+                       block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
+                       profile: Optional[Profile] = None, stream=None) -> BatchResult:
+    """Batched distance-1 coloring of independent graphs (see pgc.h)."""
+    vo, no = _Arr64(vtx_off, "vtx_off"), _Arr64(nnz_off, "nnz_off")
+    rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
+    G = vo.n - 1
+    if G < 0 or no.n != G + 1:
+        raise ValueError("vtx_off and nnz_off must have G + 1 entries")
+    N = rp.n - G
+    dev = rp.device or vo.device
+    if colors is None:
+        colors = _alloc_colors(N, dev)
+    if rounds_per_graph is None:
+        rounds_per_graph = _alloc_colors(G, dev)
+    if colors_per_graph is None:
+        colors_per_graph = _alloc_colors(G, dev)
+    co = _Arr(colors, "colors")
+    gr, gc = _Arr(rounds_per_graph, "rounds_per_graph"), _Arr(colors_per_graph, "colors_per_graph")
+    o, keep = _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm,
+                         timeout_ms, profile)
+    rounds = ctypes.c_int32(0)
+    with _device_ctx(dev):
+        st = lib().pgc_color_d1_batch(G, vo.ptr, no.ptr, rp.ptr, ci.ptr if ci.n else None,
+                                      ctypes.c_uint64(seed), co.ptr, gr.ptr, gc.ptr,
+                                      ctypes.byref(rounds), ctypes.byref(o),
+                                      _stream_handle(stream, dev))
+    _check(st)
+    _finish_profile(profile, keep, rounds.value)
+    return BatchResult(colors, rounds_per_graph, colors_per_graph, rounds.value)
 
 
 def pgc_release():

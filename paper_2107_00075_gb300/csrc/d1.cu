@@ -1,584 +1,10 @@
-// d1.cu -- distance-1 coloring: kernels and the pgc_color_d1 entry point.
-//
-// Method (Bogle et al., Sec. 3.2-3.3, Alg. 1-4), round-synchronous form:
-//   round 1       every vertex holds tentative color 1; detection decides;
-//   round r >= 2  assign: each worklist vertex takes the smallest color not
-//                 committed in its neighborhood (first fit, Alg. 1);
-//                 detect: a worklist vertex loses if a neighbor holds the
-//                 same color and has priority (Alg. 3 + Alg. 4); winners
-//                 commit, losers form the next worklist.
-//
-// How the GPU computes exactly that, with less work than re-reading every
-// worklist vertex's adjacency each round:
-//   * Detection only needs the neighbors that have priority over v (Alg. 4
-//     recolors the lower-priority end of a conflict), so setup builds, per
-//     vertex, the list H(v) = {u in N(v) : key(u) > key(v)}.  Every edge is
-//     in exactly one list, and hubs -- which stay on the worklist for many
-//     rounds -- have short lists.  A committed neighbor never holds v's
-//     tentative color (first fit excluded it), so v loses iff some u in H(v)
-//     currently holds v's tentative color.
-//   * First fit reads a per-vertex set of forbidden colors: one 64-bit word
-//     for colors 1..64 and, for vertices of degree >= 64, an overflow bitmap
-//     up to color deg(v)+1 (a first-fit color never exceeds deg(v)+1).  When
-//     a vertex commits color c it sets bit c in its neighbors' sets ("push");
-//     each vertex pushes once, so the total push work is one pass over the
-//     adjacency.
-//
-// Color encoding in col[]: > 0 committed; < 0 tentative (-t) for a vertex
-// on the current worklist.  Every uncolored vertex is on the worklist, so
-// |col[u]| is u's current color during detection; a winner flips its own
-// sign in place without disturbing concurrent readers.
-//
-// Work decomposition (no thread waits for another; no result depends on it):
-//   detect, by |H(v)|: up to 32 entries one thread per vertex; up to 1024
-//   one warp per vertex; longer lists one thread block per vertex.  Scans
-//   step through the list one entry per thread, loading the next step's ids
-//   while the current step's colors are gathered, and a loser stops at the
-//   step that finds its conflict.  Setup cuts long rows into 512-entry items
-//   and push into 128-entry items, one warp each (no decision depends on
-//   them).
-// The round loop runs on the device: a CUDA graph with a conditional WHILE
-// node around {assign, detect, push}; the last block of detect updates the
-// round state and sets the loop condition.
-#include "runtime.h"
-#include "device_common.cuh"
-
-#include <algorithm>
-#include <cstring>
-#include <functional>
-#include <memory>
-#include <unordered_map>
+// d1.cu -- pgc_color_d1: distance-1 coloring of one graph (Sec. 3.2-3.3).
+// The engine (kernels and device-side round loop) is in d1_engine.cuh; this
+// file adds argument checks, host-buffer staging and optional validation.
+#include "d1_engine.cuh"
 
 namespace pgc {
-std::vector<std::function<void()>>& release_hooks();
-
 namespace d1 {
-
-// detect tiers by |H(v)|: up to det_s one thread; up to det_m one warp;
-// longer lists one block (pgc_opts mid/hub_degree, defaults 32 and 1024)
-constexpr int kPushItem = 128;  // push: adjacency items of this length
-constexpr int kBuildS = 32;     // setup: degree up to this: one thread
-constexpr int kBuildM = 512;    // setup: degree up to this: one warp
-constexpr int kBuildItem = 512; // setup: adjacency items of this length
-constexpr int kInlinePush = 32; // S-tier winners up to this degree push inline
-
-enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3 };
-
-struct State {
-    int round;        // round being executed (1-based)
-    int done;         // 1 once the loop has ended
-    int status;       // ST_*
-    int max_color;
-    int ns[2];        // S-tier worklist sizes per parity
-    int nm[2];        // M-tier worklist sizes
-    int nl[2];        // L-tier worklist sizes
-    int bs, bm, bc;   // setup: vertices (S, M) and items (C) per degree class
-    int push_cnt;     // push work items queued this round
-    unsigned blocks_done;
-    unsigned l_next;  // dynamic index into the L-tier worklist
-    unsigned long long s_next;  // sum of degrees of the next worklist
-    unsigned long long h_next;  // sum of |H(v)| over the next worklist
-    unsigned long long h_first; // sum of |H(v)| over all vertices
-    unsigned long long t0;      // globaltimer at start
-};
-
-struct Problem {
-    const int* row_ptr;
-    const int* col_idx;
-    int* col;
-    int* deg;
-    int* hlen;
-    int* hadj;                 // H(v) stored at hadj[row_ptr[v] ...]
-    unsigned long long* bm0;   // forbidden colors 1..64, one word per vertex
-    unsigned* bmx;             // forbidden colors 65..deg+1 (deg >= 64)
-    int* ws[2];                // S-tier worklists per parity
-    int* wm[2];                // M-tier worklists
-    int* wl[2];                // L-tier worklists
-    int2* items;               // setup: (vertex, item) list for long rows
-    int2* push_q;              // (vertex, item) push work
-    long long* trace_w;
-    long long* trace_s;
-    long long* trace_h;
-    State* st;
-    unsigned long long seed;
-    unsigned long long timeout_ns;
-    int trace_cap;
-    int n;
-    int use_deg;
-    int max_rounds;
-    int det_s;
-    int det_m;
-};
-
-// key(u) > key(v), hashing only when the degree term does not decide.
-__device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v,
-                                       unsigned long long seed, bool use_deg) {
-    if (use_deg && du != dv) return du > dv;
-    const uint64_t hu = prio_hash(seed, (uint32_t)u);
-    if (hu != hv) return hu < hv;
-    return u < v;
-}
-
-__device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
-// Forbid color c for u.  Setting bits of an already-colored vertex is
-// harmless (its set is never read again), so colors 1..64 need no check and
-// the update is a fire-and-forget reduction.
-__device__ __forceinline__ void push_color(const Problem& P, int u, int c) {
-    if (c <= 64) {
-        atomicOr(P.bm0 + u, 1ull << (c - 1));
-        return;
-    }
-    const int ru = __ldg(P.row_ptr + u), du = __ldg(P.row_ptr + u + 1) - ru;
-    if (c - 1 > du) return;   // u's own first fit never reaches c
-    const int b = c - 65;
-    atomicOr(P.bmx + bitmap_offset(ru, u) + (b >> 5), 1u << (b & 31));
-}
-
-// ---------------------------------------------------------------------------
-// setup 1: degrees, tentative color 1, empty forbidden sets, degree classes
-// ---------------------------------------------------------------------------
-__global__ void d1_classify(const Problem* __restrict__ Pp) {
-    extern __shared__ int smem[];
-    const Problem& P = *Pp;
-    State* st = P.st;
-    const int warp = threadIdx.x >> 5;
-    WarpAppend as = {smem + warp * 128, 0}, am = {smem + warp * 128 + 64, 0};
-    const int n = P.n;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
-         wbase += stride) {
-        const long long i = wbase + lane_id();
-        const bool valid = i < n;
-        int d = -1;
-        if (valid) {
-            const int r0 = __ldg(P.row_ptr + i);
-            d = __ldg(P.row_ptr + i + 1) - r0;
-            P.deg[i] = d;
-            P.col[i] = -1;
-            P.hlen[i] = 0;
-            P.bm0[i] = 0ull;
-            if (d >= 64) {
-                unsigned* b = P.bmx + bitmap_offset(r0, (int)i);
-                for (int w = 0; w <= (d >> 5); ++w) b[w] = 0u;
-            }
-            if (d > kBuildM) {
-                const int nit = ceil_div(d, kBuildItem);
-                const int base = atomicAdd(&st->bc, nit);
-                for (int k = 0; k < nit; ++k) P.items[base + k] = make_int2((int)i, k);
-            }
-        }
-        wa_push(as, valid && d <= kBuildS, (int)i, P.ws[0], &st->bs);
-        wa_push(am, valid && d > kBuildS && d <= kBuildM, (int)i, P.wm[0], &st->bm);
-    }
-    wa_flush(as, P.ws[0], &st->bs);
-    wa_flush(am, P.wm[0], &st->bm);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->round = 1;
-        st->t0 = global_ns();
-        if (P.trace_cap > 0) {
-            P.trace_w[0] = n;
-            P.trace_s[0] = __ldg(P.row_ptr + n);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// setup 2: H(v) = neighbors with higher priority, stored at hadj[row_ptr[v]]
-// ---------------------------------------------------------------------------
-__global__ void d1_build(const Problem* __restrict__ Pp) {
-    const Problem& P = *Pp;
-    State* st = P.st;
-    const int* __restrict__ rp = P.row_ptr;
-    const int* __restrict__ ci = P.col_idx;
-    const int* __restrict__ dg = P.deg;
-    const unsigned long long seed = P.seed;
-    const bool use_deg = P.use_deg != 0;
-    const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
-    const int nS = st->bs, nM = st->bm, nC = st->bc;
-    unsigned long long my_h = 0ull;
-
-    // long adjacency: one warp per 512-entry item; positions by atomicAdd
-    for (int q = gw; q < nC; q += nw) {
-        const int2 it = P.items[q];
-        const int v = it.x;
-        const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
-        const uint64_t hv = prio_hash(seed, (uint32_t)v);
-        const int e0 = it.y * kBuildItem, e1 = min(d, e0 + kBuildItem);
-        for (int base = e0; base < e1; base += 32) {
-            const int e = base + lane;
-            int u = -1;
-            bool keep = false;
-            if (e < e1) {
-                u = __ldg(ci + beg + e);
-                keep = u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg);
-            }
-            const unsigned m = __ballot_sync(kFullMask, keep);
-            if (m == 0u) continue;
-            int pos = 0;
-            if (lane == 0) pos = atomicAdd(P.hlen + v, __popc(m));
-            pos = __shfl_sync(kFullMask, pos, 0);
-            if (keep) P.hadj[beg + pos + __popc(m & ((1u << lane) - 1u))] = u;
-            if (lane == 0) my_h += (unsigned long long)__popc(m);
-        }
-    }
-
-    // medium degree: one warp per vertex, ordered compaction by ballot
-    for (int i = gw; i < nM; i += nw) {
-        const int v = P.wm[0][i];
-        const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
-        const uint64_t hv = prio_hash(seed, (uint32_t)v);
-        int pos = 0;
-        for (int base = 0; base < d; base += 32) {
-            const int e = base + lane;
-            int u = -1;
-            bool keep = false;
-            if (e < d) {
-                u = __ldg(ci + beg + e);
-                keep = u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg);
-            }
-            const unsigned m = __ballot_sync(kFullMask, keep);
-            if (keep) P.hadj[beg + pos + __popc(m & ((1u << lane) - 1u))] = u;
-            pos += __popc(m);
-        }
-        if (lane == 0) {
-            P.hlen[v] = pos;
-            my_h += (unsigned long long)pos;
-        }
-    }
-
-    // small degree: one thread per vertex
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += stride) {
-        const int v = P.ws[0][i];
-        const int beg = __ldg(rp + v), end = __ldg(rp + v + 1), d = end - beg;
-        const uint64_t hv = prio_hash(seed, (uint32_t)v);
-        int pos = beg;
-        for (int e = beg; e < end; ++e) {
-            const int u = __ldg(ci + e);
-            if (u != v && higher(__ldg(dg + u), u, d, hv, v, seed, use_deg)) P.hadj[pos++] = u;
-        }
-        P.hlen[v] = pos - beg;
-        my_h += (unsigned long long)(pos - beg);
-    }
-    my_h = warp_sum(my_h);
-    if (lane == 0 && my_h) atomicAdd(&st->h_first, my_h);
-}
-
-// Append v to the worklist of its H-list tier (all 32 lanes call).
-struct TierAppend {
-    WarpAppend s, m;
-};
-
-__device__ __forceinline__ void tier_push(const Problem& P, TierAppend& a, bool pred, int v,
-                                          int hl, int p) {
-    State* st = P.st;
-    wa_push(a.s, pred && hl <= P.det_s, v, P.ws[p], &st->ns[p]);
-    wa_push(a.m, pred && hl > P.det_s && hl <= P.det_m, v, P.wm[p], &st->nm[p]);
-    if (pred && hl > P.det_m) P.wl[p][atomicAdd(&st->nl[p], 1)] = v;
-}
-
-// ---------------------------------------------------------------------------
-// setup 3: round-1 worklists by |H(v)|
-// ---------------------------------------------------------------------------
-__global__ void d1_tier(const Problem* __restrict__ Pp) {
-    extern __shared__ int smem[];
-    const Problem& P = *Pp;
-    const int warp = threadIdx.x >> 5;
-    TierAppend a = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
-    const int n = P.n;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
-         wbase += stride) {
-        const long long i = wbase + lane_id();
-        const bool valid = i < n;
-        const int hl = valid ? P.hlen[i] : 0;
-        tier_push(P, a, valid, (int)i, hl, 1);
-    }
-    wa_flush(a.s, P.ws[1], &P.st->ns[1]);
-    wa_flush(a.m, P.wm[1], &P.st->nm[1]);
-}
-
-// ---------------------------------------------------------------------------
-// assign: first fit from the forbidden-color set
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void assign_one(const Problem& P, int v) {
-    const unsigned long long w0 = P.bm0[v];
-    int t;
-    if (w0 != ~0ull) {
-        t = __ffsll((long long)~w0);
-    } else {   // colors 1..64 all taken: deg(v) >= 64, scan the overflow bitmap
-        const int r0 = __ldg(P.row_ptr + v);
-        const int words = (__ldg(P.deg + v) >> 5) + 1;
-        const unsigned* b = P.bmx + bitmap_offset(r0, v);
-        int w = 0;
-        unsigned word = b[0];
-        while (word == kFullMask && w + 1 < words) word = b[++w];
-        t = 64 + w * 32 + __ffs(~word);
-    }
-    P.col[v] = -t;
-}
-
-__global__ void d1_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
-                          int use_cond) {
-    const Problem& P = *Pp;
-    State* st = P.st;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // The loop continues only if this round's detect says so: should its
-        // round control ever not run, the device loop ends instead of spinning.
-        if (use_cond) cudaGraphSetConditional(h, 0u);
-        st->push_cnt = 0;   // the previous round's push kernel has finished
-    }
-    const int cp = *(volatile int*)&st->round & 1;
-    const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nl[cp];
-    const long long total = (long long)n0 + n1 + n2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int v = i < n0 ? P.ws[cp][i]
-                    : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
-        assign_one(P, v);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// detect + commit + compact + inline push (+ round control in the last block)
-// ---------------------------------------------------------------------------
-__device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, int use_cond) {
-    State* st = P.st;
-    const int r = st->round;
-    const int cp = r & 1, np = cp ^ 1;
-    const long long cur = (long long)st->ns[cp] + st->nm[cp] + st->nl[cp];
-    const long long nxt = (long long)*(volatile int*)&st->ns[np] + *(volatile int*)&st->nm[np] +
-                          *(volatile int*)&st->nl[np];
-    if (r < P.trace_cap) {
-        P.trace_w[r] = nxt;
-        P.trace_s[r] = (long long)*(volatile unsigned long long*)&st->s_next;
-        P.trace_h[r] = (long long)*(volatile unsigned long long*)&st->h_next;
-    }
-    if (r == 1 && P.trace_cap > 0) P.trace_h[0] = (long long)st->h_first;
-    int done = 0, status = ST_OK;
-    if (nxt == 0) {
-        done = 1;
-    } else if (nxt >= cur) {
-        done = 1;
-        status = ST_NO_PROGRESS;
-    } else if (r >= P.max_rounds) {
-        done = 1;
-        status = ST_MAX_ROUNDS;
-    } else if (global_ns() - st->t0 > P.timeout_ns) {
-        done = 1;
-        status = ST_TIMEOUT;
-    }
-    if (!done) {
-        st->ns[cp] = st->nm[cp] = st->nl[cp] = 0;
-        st->round = r + 1;
-        st->s_next = 0ull;
-        st->h_next = 0ull;
-    }
-    st->status = status;
-    st->done = done;
-    st->blocks_done = 0u;
-    st->l_next = 0u;
-    __threadfence();
-    if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
-}
-
-// Queue the push of v's color: ceil(deg / kPushItem) work items.
-__device__ __forceinline__ void queue_push(const Problem& P, int v, int d) {
-    const int nit = ceil_div(d, kPushItem);
-    const int base = atomicAdd(&P.st->push_cnt, nit);
-    for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
-}
-
-// Warp-wide: does any of the H-list entries [e0, e1) of v (starting at
-// hadj[beg]) currently hold color t?  32 entries per step; the ids of the
-// next step are loaded before this step's colors are compared.
-__device__ __forceinline__ bool warp_conflict(const Problem& P, int beg, int e0, int e1, int t) {
-    const int lane = lane_id();
-    int nxt = e0 + lane < e1 ? __ldg(P.hadj + beg + e0 + lane) : -1;
-    for (int base = e0; base < e1; base += 32) {
-        const int u = nxt;
-        const int e = base + 32 + lane;
-        nxt = e < e1 ? __ldg(P.hadj + beg + e) : -1;
-        if (__any_sync(kFullMask, u >= 0 && abs(P.col[u]) == t)) return true;
-    }
-    return false;
-}
-
-__global__ void d1_detect(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
-                          int use_cond) {
-    extern __shared__ int smem[];
-    const Problem& P = *Pp;
-    State* st = P.st;
-    const int r = *(volatile int*)&st->round;
-    const int cp = r & 1, np = cp ^ 1;
-    const int nS = st->ns[cp], nM = st->nm[cp], nL = st->nl[cp];
-    const int* __restrict__ rp = P.row_ptr;
-    const int* __restrict__ ci = P.col_idx;
-    const int* __restrict__ ha = P.hadj;
-    int* col = P.col;
-    const int lane = lane_id();
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
-    int my_max = 0;
-    unsigned long long my_s = 0ull, my_h = 0ull;
-    TierAppend app = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
-
-    // --- L tier: one block per vertex, 4 entries per thread per step ---
-    __shared__ int s_idx;
-    if (nL > 0) {
-        for (;;) {
-            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&st->l_next, 1u);
-            __syncthreads();
-            const int i = s_idx;
-            if (i >= nL) break;
-            const int v = P.wl[cp][i];
-            const int beg = __ldg(rp + v);
-            const int hl = P.hlen[v];
-            const int t = -col[v];
-            bool lose = false;
-            int nxt = (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
-            for (int base = 0; base < hl; base += blockDim.x) {
-                const int u = nxt;
-                const int e = base + blockDim.x + threadIdx.x;
-                nxt = e < hl ? __ldg(ha + beg + e) : -1;
-                if (__syncthreads_or(u >= 0 && abs(col[u]) == t)) {
-                    lose = true;
-                    break;
-                }
-            }
-            if (threadIdx.x == 0) {
-                const int d = __ldg(rp + v + 1) - beg;
-                if (lose) {
-                    P.wl[np][atomicAdd(&st->nl[np], 1)] = v;
-                    my_s += (unsigned long long)d;
-                    my_h += (unsigned long long)hl;
-                } else {
-                    col[v] = t;
-                    my_max = max(my_max, t);
-                    queue_push(P, v, d);
-                }
-            }
-            __syncthreads();
-        }
-    }
-
-    // --- M tier: one warp per vertex ---
-    for (int i = gw; i < nM; i += nw) {
-        const int v = P.wm[cp][i];
-        const int beg = __ldg(rp + v);
-        const int hl = P.hlen[v];
-        const int t = -col[v];
-        const bool lose = warp_conflict(P, beg, 0, hl, t);
-        if (lane == 0) {
-            const int d = __ldg(rp + v + 1) - beg;
-            if (lose) {
-                my_s += (unsigned long long)d;
-                my_h += (unsigned long long)hl;
-            } else {
-                col[v] = t;
-                my_max = max(my_max, t);
-                queue_push(P, v, d);
-            }
-        }
-        tier_push(P, app, lose && lane == 0, v, hl, np);
-    }
-
-    // --- S tier: one thread per vertex ---
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < nS;
-         wbase += stride) {
-        const long long i = wbase + lane;
-        bool lose = false;
-        int v = -1, hl = 0;
-        if (i < nS) {
-            v = P.ws[cp][i];
-            const int beg = __ldg(rp + v), d = __ldg(rp + v + 1) - beg;
-            hl = P.hlen[v];
-            const int t = -col[v];
-            int nxt = hl > 0 ? __ldg(ha + beg) : -1;
-            for (int e = 0; e < hl; ++e) {
-                const int u = nxt;
-                nxt = e + 1 < hl ? __ldg(ha + beg + e + 1) : -1;
-                if (abs(col[u]) == t) {
-                    lose = true;
-                    break;
-                }
-            }
-            if (lose) {
-                my_s += (unsigned long long)d;
-                my_h += (unsigned long long)hl;
-            } else {
-                col[v] = t;
-                my_max = max(my_max, t);
-                if (d <= kInlinePush) {
-                    for (int e = beg; e < beg + d; ++e) {
-                        const int u = __ldg(ci + e);
-                        if (u != v) push_color(P, u, t);
-                    }
-                } else {
-                    queue_push(P, v, d);
-                }
-            }
-        }
-        tier_push(P, app, lose, v, hl, np);
-    }
-    wa_flush(app.s, P.ws[np], &st->ns[np]);
-    wa_flush(app.m, P.wm[np], &st->nm[np]);
-
-    // --- per-warp totals ---
-    my_max = warp_max(my_max);
-    my_s = warp_sum(my_s);
-    my_h = warp_sum(my_h);
-    if (lane == 0) {
-        if (my_max > 0) atomicMax(&st->max_color, my_max);
-        if (my_s > 0) atomicAdd(&st->s_next, my_s);
-        if (my_h > 0) atomicAdd(&st->h_next, my_h);
-    }
-
-    // --- last block runs the round control ---
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&st->blocks_done, 1u);
-        s_last = ticket == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        round_control(P, h, use_cond);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// push: winners' colors into the forbidden sets of their neighbors
-// ---------------------------------------------------------------------------
-__global__ void d1_push(const Problem* __restrict__ Pp) {
-    const Problem& P = *Pp;
-    const int nq = *(volatile int*)&P.st->push_cnt;
-    const int lane = lane_id(), wpb = blockDim.x >> 5;
-    for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < nq; q += gridDim.x * wpb) {
-        const int2 item = P.push_q[q];
-        const int v = item.x;
-        const int c = P.col[v];
-        const int r0 = __ldg(P.row_ptr + v), r1 = __ldg(P.row_ptr + v + 1);
-        const int beg = r0 + item.y * kPushItem, end = min(beg + kPushItem, r1);
-        for (int base = beg; base < end; base += 128) {
-            int u[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int e = base + j * 32 + lane;
-                u[j] = e < end ? __ldg(P.col_idx + e) : -1;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (u[j] >= 0 && u[j] != v) push_color(P, u[j], c);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // optional input validation (PGC_VALIDATE): shape and id range
@@ -599,275 +25,33 @@ __global__ void d1_validate_ids(const int* __restrict__ rp, const int* __restric
         if ((unsigned)ci[e] >= (unsigned)n) atomicOr(bad, 2);
 }
 
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
-struct Context {
-    std::mutex mu;
-    DeviceInfo dev;
-    DevBuf deg, hlen, hadj, bm0, bmx, ws, wm, wl, items, pushq, state, problem, trace, stage_rp,
-        stage_ci, stage_col, flag;
-    HostBuf h_problem, h_state, h_misc;
-    int trace_cap = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle handle = 0;
-    int g_grid = 0, g_block = 0;
-
-    void destroy_graph() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
-        g_grid = 0;
-    }
+// Staging buffers for host-memory arguments (per device).
+struct Staging {
+    DevBuf rp, ci, col, flag;
     void release() {
-        destroy_graph();
-        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &ws, &wm, &wl, &items, &pushq, &state,
-                          &problem, &trace, &stage_rp, &stage_ci, &stage_col, &flag})
-            b->release();
-        for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
-        trace_cap = 0;
+        for (DevBuf* b : {&rp, &ci, &col, &flag}) b->release();
     }
 };
 
-static std::mutex g_ctx_mu;
-static std::unordered_map<int, std::unique_ptr<Context>>& contexts() {
-    static std::unordered_map<int, std::unique_ptr<Context>> m;
-    return m;
-}
-
-static Context* get_context(int device) {
-    std::lock_guard<std::mutex> lk(g_ctx_mu);
-    auto& m = contexts();
+static Staging& staging_for(int device) {
+    static std::mutex mu;
+    static std::unordered_map<int, std::unique_ptr<Staging>> m;
+    std::lock_guard<std::mutex> lk(mu);
     auto it = m.find(device);
-    if (it != m.end()) return it->second.get();
-    static bool hooked = false;
-    if (!hooked) {
-        hooked = true;
+    if (it != m.end()) return *it->second;
+    if (m.empty()) {
         release_hooks().push_back([] {
-            std::lock_guard<std::mutex> lk2(g_ctx_mu);
+            std::lock_guard<std::mutex> lk2(mu);
             int cur = 0;
             cudaGetDevice(&cur);
-            auto f = contexts().find(cur);
-            if (f != contexts().end()) {
-                std::lock_guard<std::mutex> lk3(f->second->mu);
-                f->second->release();
-            }
+            auto f = m.find(cur);
+            if (f != m.end()) f->second->release();
         });
     }
-    auto c = std::make_unique<Context>();
-    Context* p = c.get();
-    m.emplace(device, std::move(c));
-    return p;
-}
-
-struct Geometry {
-    int grid, block;
-    size_t smem;   // two warp appenders per warp
-};
-
-static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
-    g->block = o.block;
-    g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
-    int per_sm = o.grid_per_sm;
-    if (per_sm == 0) {
-        int a = 0, b = 0;
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, d1_detect, o.block, g->smem));
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, d1_build, o.block, 0));
-        per_sm = std::max(1, std::min(a, b));
-    }
-    g->grid = cx.dev.num_sms * per_sm;
-    return PGC_OK;
-}
-
-static cudaKernelNodeParams knode(void* func, const Geometry& g, size_t smem, void** args) {
-    cudaKernelNodeParams k = {};
-    k.func = func;
-    k.gridDim = dim3(g.grid);
-    k.blockDim = dim3(g.block);
-    k.sharedMemBytes = (unsigned)smem;
-    k.kernelParams = args;
-    return k;
-}
-
-static pgc_status build_graph(Context& cx, const Geometry& g) {
-    cx.destroy_graph();
-    Problem* dP = cx.problem.as<Problem>();
-    PGC_CUDA(cudaGraphCreate(&cx.graph, 0));
-    PGC_CUDA(cudaGraphConditionalHandleCreate(&cx.handle, cx.graph, 0u, cudaGraphCondAssignDefault));
-    int use_cond = 1;
-    cudaGraphConditionalHandle hnd = cx.handle;
-    void* p_args[] = {&dP};
-    void* c_args[] = {&dP, &hnd, &use_cond};
-
-    cudaMemsetParams ms = {};
-    ms.dst = cx.state.ptr;
-    ms.value = 0;
-    ms.elementSize = 4;
-    ms.width = sizeof(State) / 4;
-    ms.height = 1;
-    cudaGraphNode_t n_ms, n_cls, n_build, n_tier, n_det, n_push, n_loop;
-    PGC_CUDA(cudaGraphAddMemsetNode(&n_ms, cx.graph, nullptr, 0, &ms));
-    cudaKernelNodeParams k_cls = knode((void*)d1_classify, g, g.smem, p_args);
-    cudaKernelNodeParams k_build = knode((void*)d1_build, g, 0, p_args);
-    cudaKernelNodeParams k_tier = knode((void*)d1_tier, g, g.smem, p_args);
-    cudaKernelNodeParams k_det = knode((void*)d1_detect, g, g.smem, c_args);
-    cudaKernelNodeParams k_push = knode((void*)d1_push, g, 0, p_args);
-    cudaKernelNodeParams k_asg = knode((void*)d1_assign, g, 0, c_args);
-    PGC_CUDA(cudaGraphAddKernelNode(&n_cls, cx.graph, &n_ms, 1, &k_cls));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_build, cx.graph, &n_cls, 1, &k_build));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_tier, cx.graph, &n_build, 1, &k_tier));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_det, cx.graph, &n_tier, 1, &k_det));
-    PGC_CUDA(cudaGraphAddKernelNode(&n_push, cx.graph, &n_det, 1, &k_push));
-
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cx.handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    PGC_CUDA(cudaGraphAddNode(&n_loop, cx.graph, &n_push, nullptr, 1, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t b_asg, b_det, b_push;
-    PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
-    PGC_CUDA(cudaGraphAddKernelNode(&b_det, body, &b_asg, 1, &k_det));
-    PGC_CUDA(cudaGraphAddKernelNode(&b_push, body, &b_det, 1, &k_push));
-
-    PGC_CUDA(cudaGraphInstantiate(&cx.exec, cx.graph, 0));
-    cx.g_grid = g.grid;
-    cx.g_block = g.block;
-    return PGC_OK;
-}
-
-static pgc_status run(Context& cx, int n, long long nnz, const int* d_rp, const int* d_ci,
-                      int* d_col, uint64_t seed, const Opts& o, cudaStream_t stream, int* rounds,
-                      int* num_colors) {
-    // --- scratch (grows, never shrinks; pointers travel in the Problem
-    //     struct, so the captured graph stays valid across calls) ---
-    const size_t bmx_words = (size_t)(nnz >> 5) + (size_t)n + 1;
-    const size_t b_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
-    const size_t q_items = (size_t)n + (size_t)(nnz / kPushItem) + 1;
-    if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
-    if (pgc_status s = cx.hlen.ensure((size_t)n * 4)) return s;
-    if (pgc_status s = cx.hadj.ensure((size_t)std::max<long long>(nnz, 1) * 4)) return s;
-    if (pgc_status s = cx.bm0.ensure((size_t)n * 8)) return s;
-    if (pgc_status s = cx.bmx.ensure(bmx_words * 4)) return s;
-    if (pgc_status s = cx.ws.ensure((size_t)n * 4 * 2)) return s;
-    if (pgc_status s = cx.wm.ensure((size_t)n * 4 * 2)) return s;
-    if (pgc_status s = cx.wl.ensure((size_t)n * 4 * 2)) return s;
-    if (pgc_status s = cx.items.ensure(b_items * sizeof(int2))) return s;
-    if (pgc_status s = cx.pushq.ensure(q_items * sizeof(int2))) return s;
-    if (pgc_status s = cx.state.ensure(sizeof(State))) return s;
-    if (pgc_status s = cx.problem.ensure(sizeof(Problem))) return s;
-    if (pgc_status s = cx.h_problem.ensure(sizeof(Problem))) return s;
-    if (pgc_status s = cx.h_state.ensure(sizeof(State))) return s;
-    const int want_trace = o.profile && o.profile->trace_cap > 0 ? o.profile->trace_cap : 0;
-    const int tcap = std::max(want_trace, 1);
-    if (cx.trace_cap < tcap) {
-        if (pgc_status s = cx.trace.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
-        if (pgc_status s = cx.h_misc.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
-        cx.trace_cap = tcap;
-    }
-
-    Geometry g;
-    if (pgc_status s = geometry(cx, o, &g)) return s;
-
-    Problem* hp = cx.h_problem.as<Problem>();
-    std::memset(hp, 0, sizeof(Problem));
-    hp->row_ptr = d_rp;
-    hp->col_idx = d_ci;
-    hp->col = d_col;
-    hp->deg = cx.deg.as<int>();
-    hp->hlen = cx.hlen.as<int>();
-    hp->hadj = cx.hadj.as<int>();
-    hp->bm0 = cx.bm0.as<unsigned long long>();
-    hp->bmx = cx.bmx.as<unsigned>();
-    for (int p = 0; p < 2; ++p) {
-        hp->ws[p] = cx.ws.as<int>() + (size_t)p * n;
-        hp->wm[p] = cx.wm.as<int>() + (size_t)p * n;
-        hp->wl[p] = cx.wl.as<int>() + (size_t)p * n;
-    }
-    hp->items = cx.items.as<int2>();
-    hp->push_q = cx.pushq.as<int2>();
-    hp->trace_w = cx.trace.as<long long>();
-    hp->trace_s = hp->trace_w + tcap;
-    hp->trace_h = hp->trace_s + tcap;
-    hp->trace_cap = want_trace;
-    hp->st = cx.state.as<State>();
-    hp->seed = seed;
-    hp->timeout_ns = (unsigned long long)o.timeout_ms * 1000000ull;
-    hp->n = n;
-    hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
-    hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
-    hp->det_s = o.mid_degree;
-    hp->det_m = o.hub_degree;
-    PGC_CUDA(cudaMemcpyAsync(cx.problem.ptr, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
-    Problem* dP = cx.problem.as<Problem>();
-
-    State* hs = cx.h_state.as<State>();
-    if (!(o.flags & PGC_HOST_LOOP)) {
-        if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block) {
-            if (pgc_status s = build_graph(cx, g)) return s;
-        }
-        PGC_CUDA(cudaGraphLaunch(cx.exec, stream));
-    } else {
-        KernelTimer kt;
-        kt.prof = o.profile;
-        kt.stream = stream;
-        const cudaGraphConditionalHandle none = 0;
-        PGC_CUDA(cudaMemsetAsync(cx.state.ptr, 0, sizeof(State), stream));
-#define PGC_TIMED(slot, name, launch)                         \
-    do {                                                      \
-        if (pgc_status s_ = kt.begin(slot, name)) return s_;  \
-        launch;                                               \
-        PGC_CUDA(cudaGetLastError());                         \
-        if (pgc_status s_ = kt.end()) return s_;              \
-    } while (0)
-        PGC_TIMED(0, "d1_classify", (d1_classify<<<g.grid, g.block, g.smem, stream>>>(dP)));
-        PGC_TIMED(1, "d1_build", (d1_build<<<g.grid, g.block, 0, stream>>>(dP)));
-        PGC_TIMED(2, "d1_tier", (d1_tier<<<g.grid, g.block, g.smem, stream>>>(dP)));
-        for (int round = 1;; ++round) {
-            if (round > 1)
-                PGC_TIMED(3, "d1_assign", (d1_assign<<<g.grid, g.block, 0, stream>>>(dP, none, 0)));
-            PGC_TIMED(4, "d1_detect",
-                      (d1_detect<<<g.grid, g.block, g.smem, stream>>>(dP, none, 0)));
-            PGC_TIMED(5, "d1_push", (d1_push<<<g.grid, g.block, 0, stream>>>(dP)));
-            PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
-            PGC_CUDA(cudaStreamSynchronize(stream));
-            if (hs->done) break;
-            if (round > hp->max_rounds + 1)
-                return fail(PGC_ERR_CUDA, "device round control did not finish the loop");
-        }
-#undef PGC_TIMED
-        kt.destroy();
-    }
-    PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
-    if (want_trace) {
-        PGC_CUDA(cudaMemcpyAsync(cx.h_misc.ptr, cx.trace.ptr, (size_t)tcap * 3 * sizeof(long long),
-                                 cudaMemcpyDeviceToHost, stream));
-    }
-    PGC_CUDA(cudaStreamSynchronize(stream));
-    if (want_trace) {
-        const long long* tw = cx.h_misc.as<long long>();
-        const long long* ts = tw + tcap;
-        const long long* th = ts + tcap;
-        const int nr = std::min(hs->round, want_trace);
-        for (int i = 0; i < want_trace; ++i) {
-            if (o.profile->trace_w) o.profile->trace_w[i] = i < nr ? tw[i] : 0;
-            if (o.profile->trace_s) o.profile->trace_s[i] = i < nr ? ts[i] : 0;
-            if (o.profile->trace_h) o.profile->trace_h[i] = i < nr ? th[i] : 0;
-        }
-    }
-    *rounds = hs->round;
-    *num_colors = hs->max_color;
-    switch (hs->status) {
-        case ST_OK: return PGC_OK;
-        case ST_NO_PROGRESS:
-            return fail(PGC_ERR_NO_CONVERGE, "a round committed no vertex (input not symmetric?)");
-        case ST_MAX_ROUNDS: return fail(PGC_ERR_NO_CONVERGE, "max_rounds reached");
-        case ST_TIMEOUT: return fail(PGC_ERR_TIMEOUT, "device round loop exceeded timeout_ms");
-        default: return fail(PGC_ERR_CUDA, "unexpected device status");
-    }
+    auto e = std::make_unique<Staging>();
+    Staging* p = e.get();
+    m.emplace(device, std::move(e));
+    return *p;
 }
 
 static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, uint64_t seed,
@@ -884,9 +68,10 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
     cudaStream_t stream = (cudaStream_t)stream_v;
     DeviceInfo dev;
     if (pgc_status s = current_device(&dev)) return s;
-    Context* cx = get_context(dev.device);
+    Engine<SingleView>* cx = engine_for<SingleView>(dev.device);
     std::lock_guard<std::mutex> lk(cx->mu);
     cx->dev = dev;
+    Staging& stg = staging_for(dev.device);
 
     const bool host_rp = is_host_pointer(row_ptr);
     const bool host_ci = col_idx ? is_host_pointer(col_idx) : host_rp;
@@ -908,30 +93,30 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
     if (nnz > 0 && !col_idx) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx");
     if (host_rp || host_ci) {
         if (host_rp) {
-            if (pgc_status s = cx->stage_rp.ensure((size_t)(n + 1) * 4)) return s;
-            PGC_CUDA(cudaMemcpyAsync(cx->stage_rp.ptr, row_ptr, (size_t)(n + 1) * 4,
+            if (pgc_status s = stg.rp.ensure((size_t)(n + 1) * 4)) return s;
+            PGC_CUDA(cudaMemcpyAsync(stg.rp.ptr, row_ptr, (size_t)(n + 1) * 4,
                                      cudaMemcpyHostToDevice, stream));
-            d_rp = cx->stage_rp.as<int>();
+            d_rp = stg.rp.as<int>();
         }
         if (host_ci && nnz > 0) {
-            if (pgc_status s = cx->stage_ci.ensure((size_t)nnz * 4)) return s;
-            PGC_CUDA(cudaMemcpyAsync(cx->stage_ci.ptr, col_idx, (size_t)nnz * 4,
+            if (pgc_status s = stg.ci.ensure((size_t)nnz * 4)) return s;
+            PGC_CUDA(cudaMemcpyAsync(stg.ci.ptr, col_idx, (size_t)nnz * 4,
                                      cudaMemcpyHostToDevice, stream));
-            d_ci = cx->stage_ci.as<int>();
+            d_ci = stg.ci.as<int>();
         }
     }
     if (host_col) {
-        if (pgc_status s = cx->stage_col.ensure((size_t)n * 4)) return s;
-        d_col = cx->stage_col.as<int>();
+        if (pgc_status s = stg.col.ensure((size_t)n * 4)) return s;
+        d_col = stg.col.as<int>();
     }
     if (o.flags & PGC_VALIDATE) {
-        if (pgc_status s = cx->flag.ensure(4)) return s;
+        if (pgc_status s = stg.flag.ensure(4)) return s;
         if (pgc_status s = cx->h_state.ensure(sizeof(State))) return s;
         int* hb = cx->h_state.as<int>();
-        PGC_CUDA(cudaMemsetAsync(cx->flag.ptr, 0, 4, stream));
-        d1_validate_offsets<<<cx->dev.num_sms * 4, 256, 0, stream>>>(d_rp, n, cx->flag.as<int>());
+        PGC_CUDA(cudaMemsetAsync(stg.flag.ptr, 0, 4, stream));
+        d1_validate_offsets<<<cx->dev.num_sms * 4, 256, 0, stream>>>(d_rp, n, stg.flag.as<int>());
         PGC_CUDA(cudaGetLastError());
-        PGC_CUDA(cudaMemcpyAsync(hb, cx->flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
+        PGC_CUDA(cudaMemcpyAsync(hb, stg.flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
         PGC_CUDA(cudaStreamSynchronize(stream));
         if (*hb) return fail(PGC_ERR_INVALID_ARG, "row_ptr is not a valid offset array");
         if (!d_ci) {
@@ -940,14 +125,16 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
             if (*hb != 0) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx with row_ptr[n] > 0");
         } else {
             d1_validate_ids<<<cx->dev.num_sms * 4, 256, 0, stream>>>(d_rp, d_ci, n,
-                                                                     cx->flag.as<int>());
+                                                                     stg.flag.as<int>());
             PGC_CUDA(cudaGetLastError());
-            PGC_CUDA(cudaMemcpyAsync(hb, cx->flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
+            PGC_CUDA(cudaMemcpyAsync(hb, stg.flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
             PGC_CUDA(cudaStreamSynchronize(stream));
             if (*hb) return fail(PGC_ERR_INVALID_ARG, "col_idx entry out of [0, n)");
         }
     }
-    pgc_status s = run(*cx, n, nnz, d_rp, d_ci, d_col, seed, o, stream, rounds, num_colors);
+    SingleView view{d_rp, d_ci};
+    pgc_status s = cx->run(view, n, nnz, d_col, nullptr, nullptr, seed, o, stream, rounds,
+                           num_colors);
     if (s != PGC_OK) return s;
     if (host_col) {
         PGC_CUDA(cudaMemcpyAsync(colors, d_col, (size_t)n * 4, cudaMemcpyDeviceToHost, stream));

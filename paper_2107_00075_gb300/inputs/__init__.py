@@ -329,18 +329,26 @@ def make_batch(graphs) -> Batch:
     return Batch(vtx_off, nnz_off, row_ptr, col_idx)
 
 
+def batch_plan(num_graphs: int = 4096, n_min: int = 100, n_max: int = 200_000, seed: int = 1):
+    """Sizes (log-uniform on [n_min, n_max]) and ER average degrees (U[2, 32])
+    of the mixed batch."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), num_graphs)).astype(np.int64)
+    degs = rng.uniform(2.0, 32.0, num_graphs)
+    return sizes, degs
+
+
+def batch_member(i: int, sizes, degs, seed: int = 1) -> CSR:
+    """Member i: a 2D 5-point grid for even i, G(n, m) for odd i."""
+    n = int(sizes[i])
+    if i % 2 == 0:
+        return grid2d(n)
+    return er(n, float(degs[i]), seed=seed * 1000003 + i)
+
+
 def batch_mixed(num_graphs: int = 4096, n_min: int = 100, n_max: int = 200_000,
                 seed: int = 1) -> Batch:
     """Even members: 2D 5-point grids; odd members: G(n, m) with average
     degree U[2, 32]; sizes log-uniform on [n_min, n_max]."""
-    rng = np.random.default_rng(seed)
-    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), num_graphs)).astype(np.int64)
-    degs = rng.uniform(2.0, 32.0, num_graphs)
-    graphs = []
-    for i in range(num_graphs):
-        n = int(sizes[i])
-        if i % 2 == 0:
-            graphs.append(grid2d(n))
-        else:
-            graphs.append(er(n, float(degs[i]), seed=seed * 1000003 + i))
-    return make_batch(graphs)
+    sizes, degs = batch_plan(num_graphs, n_min, n_max, seed)
+    return make_batch([batch_member(i, sizes, degs, seed) for i in range(num_graphs)])

@@ -3,7 +3,27 @@ worker processes: no CUDA here)."""
 import oracle
 from paper_2107_00075_gb300 import inputs as gen
 
+import hashlib
+
+import numpy as np
+
 CASES = ("rmat24_d1", "stencil128_d2", "bip_pd2")
+BATCH_GRAPHS = 4096
+
+
+def digest(colors) -> str:
+    return hashlib.sha256(np.ascontiguousarray(colors, dtype=np.int32).tobytes()).hexdigest()
+
+
+def batch_oracle_job(indices):
+    """Oracle on members of the 4096-graph batch: (index, digest, rounds, colors)."""
+    sizes, degs = gen.batch_plan(BATCH_GRAPHS)
+    out = []
+    for i in indices:
+        g = gen.batch_member(i, sizes, degs)
+        r = oracle.color_d1(g.row_ptr, g.col_idx, seed=1)
+        out.append((i, digest(r.colors), r.rounds, r.num_colors))
+    return out
 
 
 def make_input(kind):

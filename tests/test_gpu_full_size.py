@@ -2,7 +2,9 @@
 
   * D1 on R-MAT scale 24 (16.8M vertices, ~521M CSR entries);
   * D2 on the 27-point stencil 128^3 (2.1M vertices, 53.6M entries);
-  * PD2 on the 4M x 1M random Jacobian pattern (rows 1 + Poisson(7)).
+  * PD2 on the 4M x 1M random Jacobian pattern (rows 1 + Poisson(7));
+  * the batched form on 4096 graphs (half 2D grids, half G(n, m) with
+    average degree U[2, 32], sizes log-uniform on [100, 200000]).
 
 The colors are compared with the oracle element by element.  The three
 oracle runs take minutes of single-threaded CPU time, so they run in
@@ -24,6 +26,18 @@ pytestmark = pytest.mark.gpu
 def oracle_futures():
     ex = ProcessPoolExecutor(max_workers=3, mp_context=mp.get_context("spawn"))
     futs = {k: ex.submit(jobs.oracle_job, k) for k in jobs.CASES}
+    yield futs
+    ex.shutdown(wait=False, cancel_futures=True)
+
+
+@pytest.fixture(scope="module")
+def batch_oracle_futures():
+    import os
+    workers = max(1, min(12, (os.cpu_count() or 4) - 3))
+    ex = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    idx = list(range(jobs.BATCH_GRAPHS))
+    chunks = [idx[k::workers * 4] for k in range(workers * 4)]
+    futs = [ex.submit(jobs.batch_oracle_job, c) for c in chunks]
     yield futs
     ex.shutdown(wait=False, cancel_futures=True)
 
@@ -80,3 +94,23 @@ def test_bipartite_pd2_bit_exact(oracle_futures):
     colors = r.colors.cpu().numpy()
     _compare(colors, r.rounds, r.num_colors, prof, oracle_futures["bip_pd2"].result())
     assert r.num_colors >= np.diff(b.row_ptr).max()
+
+
+def test_batch4096_bit_exact(batch_oracle_futures):
+    import torch
+    import paper_2107_00075_gb300 as pgc
+    from paper_2107_00075_gb300 import inputs as gen
+    b = gen.batch_mixed(jobs.BATCH_GRAPHS)
+    t = lambda a: torch.from_numpy(a).cuda()
+    r = pgc.pgc_color_d1_batch(t(b.vtx_off), t(b.nnz_off), t(b.row_ptr), t(b.col_idx), seed=1)
+    colors = r.colors.cpu().numpy()
+    gr = r.rounds_per_graph.cpu().numpy()
+    gc = r.colors_per_graph.cpu().numpy()
+    seen = 0
+    for f in batch_oracle_futures:
+        for i, dig, rounds, ncol in f.result():
+            a, z = int(b.vtx_off[i]), int(b.vtx_off[i + 1])
+            assert jobs.digest(colors[a:z]) == dig, f"graph {i}"
+            assert gr[i] == rounds and gc[i] == ncol, f"graph {i}"
+            seen += 1
+    assert seen == jobs.BATCH_GRAPHS
