@@ -192,6 +192,34 @@ pgc_status pgc_color_d1_batch(int32_t G, const int64_t *vtx_off, const int64_t *
                               int32_t *colors, int32_t *rounds_per_g, int32_t *ncolors_per_g,
                               int32_t *rounds, const pgc_opts *opts, void *stream);
 
+/*
+ * pgc_color_d1_noalloc -- pgc_color_d1 for callers that must not have the
+ * library allocate device memory (the paper has no counterpart; this is a
+ * deployment variant).  Callers whose device memory is owned by another
+ * allocator, or who cannot accept the device-wide synchronisation of
+ * cudaFree, get the same colors, rounds and color count as pgc_color_d1 with
+ * no cudaMalloc, cudaFree or other allocating call.  All scratch is one
+ * fixed array of about 4 MB in device memory that every GPU loading the
+ * library keeps until the process exits.
+ *   Limits: n <= 32768 and row_ptr[n] <= 524288; larger inputs are rejected
+ *           with PGC_ERR_INVALID_ARG before any work is launched.
+ *   row_ptr, col_idx, colors: DEVICE memory only (host pointers are rejected,
+ *           since staging them would need an allocation); layout as
+ *           pgc_color_d1.  rounds, num_colors: host outputs.
+ *   flags:  PGC_NO_DEGREE_RULE or 0 (other options are fixed to defaults).
+ *   The first call on a device looks up the array's device address (once per
+ *           device, with that device current); make that first call before
+ *           any stream capture.
+ *   Every call reuses the same array and the array keeps the previous call's
+ *           contents; the call clears what must start at zero.  Two calls
+ *           whose GPU work overlapped would race on the array: calls take a
+ *           process-wide lock and synchronize `stream` before returning, so
+ *           calls made through this function never overlap.
+ */
+pgc_status pgc_color_d1_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                uint64_t seed, int32_t *colors, int32_t *rounds,
+                                int32_t *num_colors, uint32_t flags, void *stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char *pgc_last_error(void);
 
