@@ -49,6 +49,7 @@
 #ifndef PGC_H
 #define PGC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -219,6 +220,75 @@ pgc_status pgc_color_d1_batch(int32_t G, const int64_t *vtx_off, const int64_t *
 pgc_status pgc_color_d1_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                                 uint64_t seed, int32_t *colors, int32_t *rounds,
                                 int32_t *num_colors, uint32_t flags, void *stream);
+
+/*
+ * Coloring server with continuous batching (the served form; the paper has
+ * no serving API).  Any host thread submits distance-1 graphs or partial
+ * distance-2 patterns; one engine thread admits them first come first
+ * served, at round-loop boundaries, when an execution slot and room for the
+ * request's device footprint (inputs + colors + scratch) in the server's
+ * HBM arena are both free.  Each active request runs the device-side round
+ * loop on its own stream, so requests overlap on the GPU; CSR and color
+ * state stay on the device for all rounds.  Colors, rounds and color counts
+ * equal those of pgc_color_d1 / pgc_color_pd2 on the request alone.
+ *
+ * Buffers passed to submit belong to the caller and must stay valid and
+ * unchanged until the request is reported done (wait, or poll with done=1).
+ * Inputs are read with cudaMemcpyDefault (host or device memory; pinned host
+ * memory keeps the upload asynchronous); colors may be host or device memory.
+ */
+typedef struct pgc_server pgc_server;
+
+typedef struct {
+    int32_t status;            /* pgc_status of the request */
+    int32_t rounds;
+    int32_t num_colors;
+    int32_t reserved;
+    int64_t t_submit_ns;       /* steady-clock stamps: submit, admission, done */
+    int64_t t_admit_ns;
+    int64_t t_done_ns;
+    int64_t footprint_bytes;   /* device bytes the request held while active */
+} pgc_request_info;
+
+typedef struct {
+    int64_t submitted, completed, rejected;
+    int32_t active, queued;
+    int64_t bytes_in_use, peak_bytes, budget_bytes;
+    int32_t max_active_seen;
+    int32_t reserved;
+} pgc_server_counters;
+
+/* A server on the current device with an HBM arena of hbm_budget_bytes
+   (allocated here) and at most max_active concurrent requests (1..256). */
+pgc_status pgc_server_create(size_t hbm_budget_bytes, int32_t max_active, pgc_server **out);
+
+/* Queue a distance-1 request (CSR as in pgc_color_d1; colors: int32[n]).
+   PGC_ERR_BUSY if its footprint exceeds the whole budget. */
+pgc_status pgc_server_submit_d1(pgc_server *srv, int32_t n, const int32_t *row_ptr,
+                                const int32_t *col_idx, uint64_t seed, int32_t *colors,
+                                int64_t *req_id);
+
+/* Queue a partial distance-2 request (arrays as in pgc_color_pd2, host
+   memory; colors: int32[n_cols]). */
+pgc_status pgc_server_submit_pd2(pgc_server *srv, int32_t n_rows, int32_t n_cols,
+                                 const int32_t *row_ptr, const int32_t *col_idx,
+                                 const int32_t *col_ptr, const int32_t *row_idx, uint64_t seed,
+                                 int32_t *colors, int64_t *req_id);
+
+/* done = 1 once finished; the request's info is then returned and its id
+   released (later calls with it give PGC_ERR_NOT_FOUND). */
+pgc_status pgc_server_poll(pgc_server *srv, int64_t req_id, int32_t *done,
+                           pgc_request_info *info);
+
+/* Block until the request is done (timeout_ms < 0: no limit; otherwise
+   PGC_ERR_TIMEOUT and the request stays pending).  Releases the id. */
+pgc_status pgc_server_wait(pgc_server *srv, int64_t req_id, int32_t timeout_ms,
+                           pgc_request_info *info);
+
+pgc_status pgc_server_stats(pgc_server *srv, pgc_server_counters *out);
+
+/* Finishes every queued and active request, then frees the server. */
+pgc_status pgc_server_destroy(pgc_server *srv);
 
 /* Message for the last error on this thread ("" if none). */
 const char *pgc_last_error(void);

@@ -52,6 +52,21 @@ class PgcOptsC(ctypes.Structure):
                 ("profile", ctypes.POINTER(PgcProfileC))]
 
 
+class RequestInfoC(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("num_colors", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("footprint_bytes", ctypes.c_int64)]
+
+
+class ServerCountersC(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("active", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("bytes_in_use", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("max_active_seen", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 @dataclass
 class Profile:
     """Per-round trace and (PGC_HOST_LOOP) per-kernel CUDA-event times."""
@@ -92,6 +107,22 @@ def lib():
         L.pgc_color_d1_batch.argtypes = [i32, p, p, p, p, u64, p, p, p, ctypes.POINTER(i32),
                                          ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_d1_batch.restype = ctypes.c_int
+        L.pgc_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(p)]
+        L.pgc_server_create.restype = ctypes.c_int
+        L.pgc_server_submit_d1.argtypes = [p, i32, p, p, u64, p, ctypes.POINTER(ctypes.c_int64)]
+        L.pgc_server_submit_d1.restype = ctypes.c_int
+        L.pgc_server_submit_pd2.argtypes = [p, i32, i32, p, p, p, p, u64, p,
+                                            ctypes.POINTER(ctypes.c_int64)]
+        L.pgc_server_submit_pd2.restype = ctypes.c_int
+        L.pgc_server_poll.argtypes = [p, ctypes.c_int64, ctypes.POINTER(i32),
+                                      ctypes.POINTER(RequestInfoC)]
+        L.pgc_server_poll.restype = ctypes.c_int
+        L.pgc_server_wait.argtypes = [p, ctypes.c_int64, i32, ctypes.POINTER(RequestInfoC)]
+        L.pgc_server_wait.restype = ctypes.c_int
+        L.pgc_server_stats.argtypes = [p, ctypes.POINTER(ServerCountersC)]
+        L.pgc_server_stats.restype = ctypes.c_int
+        L.pgc_server_destroy.argtypes = [p]
+        L.pgc_server_destroy.restype = ctypes.c_int
         L.pgc_last_error.restype = ctypes.c_char_p
         L.pgc_status_string.argtypes = [ctypes.c_int]
         L.pgc_status_string.restype = ctypes.c_char_p
@@ -342,3 +373,101 @@ def pgc_release():
 
 def pgc_version() -> str:
     return lib().pgc_version().decode()
+
+
+@dataclass
+class RequestInfo:
+    status: int
+    rounds: int
+    num_colors: int
+    t_submit_ns: int
+    t_admit_ns: int
+    t_done_ns: int
+    footprint_bytes: int
+
+    @property
+    def latency_s(self) -> float:
+        return (self.t_done_ns - self.t_submit_ns) * 1e-9
+
+
+class PgcServer:
+    """pgc_server_* (see pgc.h): continuous-batching coloring server.
+
+    Keeps every submitted buffer alive until its request is reported done."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 16, device=None):
+        import contextlib
+        ctx = _device_ctx(device) if device is not None else contextlib.nullcontext()
+        self._h = ctypes.c_void_p()
+        with ctx:
+            _check(lib().pgc_server_create(hbm_budget_bytes, max_active, ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit_d1(self, row_ptr, col_idx, seed: int = 1, colors=None) -> int:
+        rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
+        n = rp.n - 1
+        if colors is None:
+            colors = np.zeros(n, dtype=np.int32)
+        co = _Arr(colors, "colors")
+        rid = ctypes.c_int64(0)
+        _check(lib().pgc_server_submit_d1(self._h, n, rp.ptr, ci.ptr if ci.n else None,
+                                          ctypes.c_uint64(seed), co.ptr, ctypes.byref(rid)))
+        self._keep[rid.value] = (rp, ci, co)
+        return rid.value
+
+    def submit_pd2(self, n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed: int = 1,
+                   colors=None) -> int:
+        arrs = [_Arr(a, nm) for a, nm in ((row_ptr, "row_ptr"), (col_idx, "col_idx"),
+                                          (col_ptr, "col_ptr"), (row_idx, "row_idx"))]
+        if colors is None:
+            colors = np.zeros(n_cols, dtype=np.int32)
+        co = _Arr(colors, "colors")
+        rid = ctypes.c_int64(0)
+        _check(lib().pgc_server_submit_pd2(self._h, n_rows, n_cols, arrs[0].ptr, arrs[1].ptr,
+                                           arrs[2].ptr, arrs[3].ptr, ctypes.c_uint64(seed),
+                                           co.ptr, ctypes.byref(rid)))
+        self._keep[rid.value] = tuple(arrs) + (co,)
+        return rid.value
+
+    def colors(self, req_id: int):
+        return self._keep[req_id][-1].obj
+
+    def _info(self, ci) -> RequestInfo:
+        return RequestInfo(ci.status, ci.rounds, ci.num_colors, ci.t_submit_ns, ci.t_admit_ns,
+                           ci.t_done_ns, ci.footprint_bytes)
+
+    def wait(self, req_id: int, timeout_ms: int = -1):
+        """Returns (colors, RequestInfo) once done."""
+        ci = RequestInfoC()
+        _check(lib().pgc_server_wait(self._h, req_id, timeout_ms, ctypes.byref(ci)))
+        keep = self._keep.pop(req_id)
+        return keep[-1].obj, self._info(ci)
+
+    def poll(self, req_id: int):
+        """None while running, else (colors, RequestInfo)."""
+        ci = RequestInfoC()
+        done = ctypes.c_int32(0)
+        st = lib().pgc_server_poll(self._h, req_id, ctypes.byref(done), ctypes.byref(ci))
+        if not done.value:
+            _check(st)
+            return None
+        keep = self._keep.pop(req_id)
+        _check(st)
+        return keep[-1].obj, self._info(ci)
+
+    def stats(self) -> dict:
+        c = ServerCountersC()
+        _check(lib().pgc_server_stats(self._h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in ServerCountersC._fields_ if f != "reserved"}
+
+    def close(self):
+        if self._h:
+            lib().pgc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

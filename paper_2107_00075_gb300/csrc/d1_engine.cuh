@@ -686,8 +686,64 @@ __global__ void d1_push(const Problem<V>* __restrict__ Pp) {
 }
 
 // ---------------------------------------------------------------------------
-// host side: one engine instance per (device, view type)
+// host side: scratch layout and one engine instance per (device, view type)
 // ---------------------------------------------------------------------------
+// Device scratch of one coloring (n vertices, nnz adjacency entries).
+struct Scratch {
+    int* deg;
+    int* hlen;
+    int* hadj;
+    unsigned long long* bm0;
+    unsigned* bmx;
+    int* ws;     // 2n: both parities
+    int* wm;
+    int* wl;
+    int2* items;
+    int2* pushq;
+};
+
+struct ScratchSizes {
+    size_t deg, hlen, hadj, bm0, bmx, list, items, pushq;
+    size_t total() const {   // with 256-byte alignment of every buffer
+        auto a = [](size_t x) { return (x + 255) / 256 * 256; };
+        return a(deg) + a(hlen) + a(hadj) + a(bm0) + a(bmx) + 3 * a(list) + a(items) + a(pushq);
+    }
+};
+
+inline ScratchSizes scratch_sizes(long long n, long long nnz) {
+    ScratchSizes z;
+    z.deg = z.hlen = (size_t)n * 4;
+    z.hadj = (size_t)std::max<long long>(nnz, 1) * 4;
+    z.bm0 = (size_t)n * 8;
+    z.bmx = ((size_t)(nnz >> 5) + (size_t)n + 1) * 4;
+    z.list = (size_t)n * 4 * 2;
+    z.items = ((size_t)n + (size_t)(nnz / kBuildItem) + 1) * sizeof(int2);
+    z.pushq = ((size_t)n + (size_t)(nnz / kPushItem) + 1) * sizeof(int2);
+    return z;
+}
+
+// Carves a scratch of scratch_sizes(n, nnz).total() bytes at base.
+inline Scratch carve_scratch(void* base, long long n, long long nnz) {
+    const ScratchSizes z = scratch_sizes(n, nnz);
+    char* p = static_cast<char*>(base);
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    Scratch sc;
+    sc.deg = reinterpret_cast<int*>(take(z.deg));
+    sc.hlen = reinterpret_cast<int*>(take(z.hlen));
+    sc.hadj = reinterpret_cast<int*>(take(z.hadj));
+    sc.bm0 = reinterpret_cast<unsigned long long*>(take(z.bm0));
+    sc.bmx = reinterpret_cast<unsigned*>(take(z.bmx));
+    sc.ws = reinterpret_cast<int*>(take(z.list));
+    sc.wm = reinterpret_cast<int*>(take(z.list));
+    sc.wl = reinterpret_cast<int*>(take(z.list));
+    sc.items = reinterpret_cast<int2*>(take(z.items));
+    sc.pushq = reinterpret_cast<int2*>(take(z.pushq));
+    return sc;
+}
 template <class V>
 struct Engine {
     std::mutex mu;
@@ -695,6 +751,7 @@ struct Engine {
     DevBuf deg, hlen, hadj, bm0, bmx, ws, wm, wl, items, pushq, state, problem, trace;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
+    int last_want_trace = 0, last_tcap = 1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
@@ -790,25 +847,48 @@ struct Engine {
         return PGC_OK;
     }
 
-    // Colors n vertices (nnz adjacency entries in total) described by view.
+    // Colors n vertices (nnz adjacency entries in total) described by view,
+    // with scratch owned by this engine; waits for the result.
     pgc_status run(const V& view, int n, long long nnz, int* d_col, int* g_rounds,
                    int* g_colors, uint64_t seed, const Opts& o, cudaStream_t stream,
                    int* rounds, int* num_colors) {
         // scratch grows, never shrinks; pointers travel in the Problem struct,
         // so the captured graph stays valid across calls
-        const size_t bmx_words = (size_t)(nnz >> 5) + (size_t)n + 1;
-        const size_t b_items = (size_t)n + (size_t)(nnz / kBuildItem) + 1;
-        const size_t q_items = (size_t)n + (size_t)(nnz / kPushItem) + 1;
-        if (pgc_status s = deg.ensure((size_t)n * 4)) return s;
-        if (pgc_status s = hlen.ensure((size_t)n * 4)) return s;
-        if (pgc_status s = hadj.ensure((size_t)std::max<long long>(nnz, 1) * 4)) return s;
-        if (pgc_status s = bm0.ensure((size_t)n * 8)) return s;
-        if (pgc_status s = bmx.ensure(bmx_words * 4)) return s;
-        if (pgc_status s = ws.ensure((size_t)n * 4 * 2)) return s;
-        if (pgc_status s = wm.ensure((size_t)n * 4 * 2)) return s;
-        if (pgc_status s = wl.ensure((size_t)n * 4 * 2)) return s;
-        if (pgc_status s = items.ensure(b_items * sizeof(int2))) return s;
-        if (pgc_status s = pushq.ensure(q_items * sizeof(int2))) return s;
+        const ScratchSizes z = scratch_sizes(n, nnz);
+        if (pgc_status s = deg.ensure(z.deg)) return s;
+        if (pgc_status s = hlen.ensure(z.hlen)) return s;
+        if (pgc_status s = hadj.ensure(z.hadj)) return s;
+        if (pgc_status s = bm0.ensure(z.bm0)) return s;
+        if (pgc_status s = bmx.ensure(z.bmx)) return s;
+        if (pgc_status s = ws.ensure(z.list)) return s;
+        if (pgc_status s = wm.ensure(z.list)) return s;
+        if (pgc_status s = wl.ensure(z.list)) return s;
+        if (pgc_status s = items.ensure(z.items)) return s;
+        if (pgc_status s = pushq.ensure(z.pushq)) return s;
+        Scratch sc;
+        sc.deg = deg.as<int>();
+        sc.hlen = hlen.as<int>();
+        sc.hadj = hadj.as<int>();
+        sc.bm0 = bm0.as<unsigned long long>();
+        sc.bmx = bmx.as<unsigned>();
+        sc.ws = ws.as<int>();
+        sc.wm = wm.as<int>();
+        sc.wl = wl.as<int>();
+        sc.items = items.as<int2>();
+        sc.pushq = pushq.as<int2>();
+        if (pgc_status s = launch(sc, view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream))
+            return s;
+        PGC_CUDA(cudaStreamSynchronize(stream));
+        return finish(o, rounds, num_colors);
+    }
+
+    // Enqueues one coloring on `stream` with caller-provided scratch (the
+    // device loop in graph mode; host-loop mode drives the rounds and
+    // therefore blocks).  The round state and trace are copied to pinned
+    // host memory on the same stream; call finish() once the stream is done.
+    pgc_status launch(const Scratch& sc, const V& view, int n, long long nnz, int* d_col,
+                      int* g_rounds, int* g_colors, uint64_t seed, const Opts& o,
+                      cudaStream_t stream) {
         if (pgc_status s = state.ensure(sizeof(State))) return s;
         if (pgc_status s = problem.ensure(sizeof(Problem<V>))) return s;
         if (pgc_status s = h_problem.ensure(sizeof(Problem<V>))) return s;
@@ -820,6 +900,8 @@ struct Engine {
             if (pgc_status s = h_misc.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
             trace_cap = tcap;
         }
+        last_want_trace = want_trace;
+        last_tcap = tcap;
 
         Geometry g;
         if (pgc_status s = geometry(o, &g)) return s;
@@ -828,18 +910,18 @@ struct Engine {
         std::memset(hp, 0, sizeof(Problem<V>));
         hp->g = view;
         hp->col = d_col;
-        hp->deg = deg.as<int>();
-        hp->hlen = hlen.as<int>();
-        hp->hadj = hadj.as<int>();
-        hp->bm0 = bm0.as<unsigned long long>();
-        hp->bmx = bmx.as<unsigned>();
+        hp->deg = sc.deg;
+        hp->hlen = sc.hlen;
+        hp->hadj = sc.hadj;
+        hp->bm0 = sc.bm0;
+        hp->bmx = sc.bmx;
         for (int p = 0; p < 2; ++p) {
-            hp->ws[p] = ws.as<int>() + (size_t)p * n;
-            hp->wm[p] = wm.as<int>() + (size_t)p * n;
-            hp->wl[p] = wl.as<int>() + (size_t)p * n;
+            hp->ws[p] = sc.ws + (size_t)p * n;
+            hp->wm[p] = sc.wm + (size_t)p * n;
+            hp->wl[p] = sc.wl + (size_t)p * n;
         }
-        hp->items = items.as<int2>();
-        hp->push_q = pushq.as<int2>();
+        hp->items = sc.items;
+        hp->push_q = sc.pushq;
         hp->g_rounds = g_rounds;
         hp->g_colors = g_colors;
         hp->trace_w = trace.as<long long>();
@@ -871,10 +953,10 @@ struct Engine {
             kt.stream = stream;
             const cudaGraphConditionalHandle none = 0;
             PGC_CUDA(cudaMemsetAsync(state.ptr, 0, sizeof(State), stream));
-#define PGC_TIMED(slot, name, launch)                         \
+#define PGC_TIMED(slot, name, launch_)                        \
     do {                                                      \
         if (pgc_status s_ = kt.begin(slot, name)) return s_;  \
-        launch;                                               \
+        launch_;                                              \
         PGC_CUDA(cudaGetLastError());                         \
         if (pgc_status s_ = kt.end()) return s_;              \
     } while (0)
@@ -903,8 +985,14 @@ struct Engine {
             PGC_CUDA(cudaMemcpyAsync(h_misc.ptr, trace.ptr, (size_t)tcap * 3 * sizeof(long long),
                                      cudaMemcpyDeviceToHost, stream));
         }
-        PGC_CUDA(cudaStreamSynchronize(stream));
-        if (want_trace) {
+        return PGC_OK;
+    }
+
+    // Reads the result of the last launch() (its stream must be complete).
+    pgc_status finish(const Opts& o, int* rounds, int* num_colors) {
+        State* hs = h_state.as<State>();
+        const int want_trace = last_want_trace, tcap = last_tcap;
+        if (want_trace && o.profile) {
             const long long* tw = h_misc.as<long long>();
             const long long* ts = tw + tcap;
             const long long* th = ts + tcap;

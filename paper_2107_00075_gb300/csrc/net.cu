@@ -674,6 +674,97 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     }
 }
 
+// ---------------------------------------------------------------------------
+// asynchronous launch with caller-provided scratch (used by the server): the
+// number of mask windows is given, so nothing waits on the device
+// ---------------------------------------------------------------------------
+size_t scratch_bytes(int n, int n_nets, int windows) {
+    auto a = [](size_t x) { return (x + 255) / 256 * 256; };
+    return a((size_t)n * 4) * 2 + a((size_t)std::max(n_nets, 1) * 4) +
+           a((size_t)windows * (size_t)std::max(n_nets, 1) * 8) + a((size_t)n * 8) * 2;
+}
+
+static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int windows,
+                               uint64_t seed, const Opts& o, cudaStream_t stream) {
+    const int n = in.n;
+    auto a = [](size_t x) { return (x + 255) / 256 * 256; };
+    char* p = static_cast<char*>(scratch);
+    int* deg = reinterpret_cast<int*>(p);
+    p += a((size_t)n * 4);
+    int* lose = reinterpret_cast<int*>(p);
+    p += a((size_t)n * 4);
+    int* flag = reinterpret_cast<int*>(p);
+    p += a((size_t)std::max(in.n_nets, 1) * 4);
+    unsigned long long* mask = reinterpret_cast<unsigned long long*>(p);
+    const size_t mask_bytes = (size_t)windows * (size_t)std::max(in.n_nets, 1) * 8;
+    p += a(mask_bytes);
+    int* wt = reinterpret_cast<int*>(p);
+    p += a((size_t)n * 8);
+    int* ww = reinterpret_cast<int*>(p);
+    if (pgc_status s = cx.state.ensure(sizeof(State))) return s;
+    if (pgc_status s = cx.problem.ensure(sizeof(Problem))) return s;
+    if (pgc_status s = cx.h_problem.ensure(sizeof(Problem))) return s;
+    if (pgc_status s = cx.h_state.ensure(sizeof(State))) return s;
+    if (pgc_status s = cx.trace.ensure(3 * sizeof(long long))) return s;
+    Geometry g;
+    if (pgc_status s = geometry(cx, o, &g)) return s;
+    Problem* hp = cx.h_problem.as<Problem>();
+    std::memset(hp, 0, sizeof(Problem));
+    hp->m_ptr = in.m_ptr;
+    hp->m_idx = in.m_idx;
+    hp->r_ptr = in.r_ptr;
+    hp->r_idx = in.r_idx;
+    hp->col = in.col;
+    hp->deg = deg;
+    hp->lose = lose;
+    hp->net_flag = flag;
+    hp->mask = mask;
+    for (int q = 0; q < 2; ++q) {
+        hp->wt[q] = wt + (size_t)q * n;
+        hp->ww[q] = ww + (size_t)q * n;
+    }
+    hp->trace_w = hp->trace_s = hp->trace_h = cx.trace.as<long long>();
+    hp->trace_cap = 0;
+    hp->st = cx.state.as<State>();
+    hp->seed = seed;
+    hp->timeout_ns = (unsigned long long)o.timeout_ms * 1000000ull;
+    hp->n = n;
+    hp->n_nets = in.n_nets;
+    hp->self = in.self;
+    hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
+    hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
+    hp->windows = windows;
+    Problem* dP = cx.problem.as<Problem>();
+    PGC_CUDA(cudaMemcpyAsync(dP, hp, sizeof(Problem), cudaMemcpyHostToDevice, stream));
+    PGC_CUDA(cudaMemsetAsync(cx.state.ptr, 0, sizeof(State), stream));
+    PGC_CUDA(cudaMemsetAsync(mask, 0, mask_bytes, stream));
+    net_init<<<g.grid, g.block, g.smem, stream>>>(dP);
+    PGC_CUDA(cudaGetLastError());
+    if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block) {
+        if (pgc_status s = build_graph(cx, g)) return s;
+    }
+    PGC_CUDA(cudaGraphLaunch(cx.exec, stream));
+    PGC_CUDA(cudaMemcpyAsync(cx.h_state.ptr, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost,
+                             stream));
+    return PGC_OK;
+}
+
+static pgc_status finish_known(Context& cx, int* rounds, int* num_colors) {
+    const State* hs = cx.h_state.as<State>();
+    *rounds = hs->round;
+    *num_colors = hs->max_color;
+    switch (hs->status) {
+        case ST_OK: return PGC_OK;
+        case ST_NO_PROGRESS:
+            return fail(PGC_ERR_NO_CONVERGE, "a round committed no vertex (inconsistent input?)");
+        case ST_MAX_ROUNDS: return fail(PGC_ERR_NO_CONVERGE, "max_rounds reached");
+        case ST_TIMEOUT: return fail(PGC_ERR_TIMEOUT, "device round loop exceeded timeout_ms");
+        case ST_OVERFLOW:
+            return fail(PGC_ERR_NO_CONVERGE, "a color above 4096 was needed (mask capacity)");
+        default: return fail(PGC_ERR_CUDA, "unexpected device status");
+    }
+}
+
 // Reads a[idx] whether a is host or device memory.
 static pgc_status read_int(const int* a, bool host, long long idx, int* out, Context& cx,
                            cudaStream_t stream) {
@@ -803,3 +894,40 @@ extern "C" pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_
         return pgc::fail(PGC_ERR_CUDA, "unknown exception");
     }
 }
+
+namespace pgc {
+namespace net {
+
+// Slot API for the server (declared in runtime.h).
+void* slot_create() { return new Context(); }
+
+void slot_destroy(void* c) {
+    auto* cx = static_cast<Context*>(c);
+    cx->release();
+    delete cx;
+}
+
+pgc_status slot_launch_pd2(void* c, void* scratch, int n_rows, int n_cols, const int* row_ptr,
+                           const int* col_idx, const int* col_ptr, const int* row_idx, int* colors,
+                           int windows, uint64_t seed, cudaStream_t stream) {
+    auto* cx = static_cast<Context*>(c);
+    if (pgc_status s = current_device(&cx->dev)) return s;
+    Input in;
+    in.n = n_cols;
+    in.n_nets = n_rows;
+    in.self = 0;
+    in.m_ptr = row_ptr;
+    in.m_idx = col_idx;
+    in.r_ptr = col_ptr;
+    in.r_idx = row_idx;
+    in.col = colors;
+    Opts o;
+    return launch_known(*cx, scratch, in, windows, seed, o, stream);
+}
+
+pgc_status slot_finish(void* c, int* rounds, int* num_colors) {
+    return finish_known(*static_cast<Context*>(c), rounds, num_colors);
+}
+
+}  // namespace net
+}  // namespace pgc

@@ -74,4 +74,15 @@ struct KernelTimer {
     void destroy();
 };
 
+// Partial distance-2 engine slots for the server (net.cu).
+namespace net {
+size_t scratch_bytes(int n, int n_nets, int windows);
+void* slot_create();
+void slot_destroy(void* slot);
+pgc_status slot_launch_pd2(void* slot, void* scratch, int n_rows, int n_cols, const int* row_ptr,
+                           const int* col_idx, const int* col_ptr, const int* row_idx, int* colors,
+                           int windows, uint64_t seed, cudaStream_t stream);
+pgc_status slot_finish(void* slot, int* rounds, int* num_colors);
+}  // namespace net
+
 }  // namespace pgc
