@@ -201,6 +201,153 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def bench_batch(pgc, inputs, torch, dev, num_graphs):
+    """The batched form vs one plain pgc_color_d1 call per graph, inputs
+    resident on the device, identical colorings checked."""
+    t0 = time.time()
+    b = inputs.batch_mixed(num_graphs, seed=SEED)
+    gen_s = time.time() - t0
+    t = lambda a: torch.from_numpy(a).to(dev)
+    vo, no, rp, ci = t(b.vtx_off), t(b.nnz_off), t(b.row_ptr), t(b.col_idx)
+    N, E = int(b.vtx_off[-1]), int(b.nnz_off[-1])
+    colors = torch.empty(N, dtype=torch.int32, device=dev)
+    gr = torch.empty(num_graphs, dtype=torch.int32, device=dev)
+    gc = torch.empty(num_graphs, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # the autotuner picks the configuration on the warm-up call
+    pgc.pgc_color_d1_batch(vo, no, rp, ci, seed=SEED, colors=colors, rounds_per_graph=gr,
+                           colors_per_graph=gc, flags=pgc.PGC_AUTOTUNE, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(reps):
+        r = pgc.pgc_color_d1_batch(vo, no, rp, ci, seed=SEED, colors=colors, rounds_per_graph=gr,
+                                   colors_per_graph=gc, flags=pgc.PGC_AUTOTUNE, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    batched_ms = ev0.elapsed_time(ev1) / reps
+    # plain: one call per graph on per-graph device arrays
+    per = []
+    for g in range(num_graphs):
+        csr = b.graph(g)
+        per.append((t(csr.row_ptr), t(csr.col_idx),
+                    torch.empty(csr.n, dtype=torch.int32, device=dev)))
+    for rp_g, ci_g, col_g in per[:8]:
+        if col_g.numel():
+            pgc.pgc_color_d1(rp_g, ci_g, seed=SEED, colors=col_g, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for rp_g, ci_g, col_g in per:
+        if col_g.numel():
+            pgc.pgc_color_d1(rp_g, ci_g, seed=SEED, colors=col_g, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = ev0.elapsed_time(ev1)
+    same = all(torch.equal(colors[int(b.vtx_off[g]):int(b.vtx_off[g + 1])], per[g][2])
+               for g in range(num_graphs))
+    return {"workload": f"{num_graphs} graphs: 2D 5-point grids and G(n,m) with avg degree "
+                        "U[2,32], n log-uniform [100, 200000]",
+            "graphs": num_graphs, "vertices": N, "entries": E, "edges": E // 2,
+            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "batched_edges_per_s": (E / 2) / (batched_ms / 1000),
+            "plain_edges_per_s": (E / 2) / (plain_ms / 1000), "identical_colors": bool(same),
+            "max_rounds": int(gr.max().item()), "gen_s": gen_s, "autotuned": True}
+
+
+def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, seed=7):
+    """Served form vs a plain FIFO of single calls, same Poisson arrivals.
+    Payloads (70% D1 R-MAT scale-matched, edge factor 8; 30% PD2 rows
+    0.8n x columns 0.2n, rows 1 + Poisson(7); n log-uniform [1K, 4M]) are
+    generated ahead into pinned host memory; every request has its own seed.
+    Latency = completion - arrival, host-to-device upload included."""
+    import threading
+    rng = np.random.default_rng(seed)
+    payloads = []
+    for i in range(n_payloads):
+        n = int(np.exp(rng.uniform(np.log(1000), np.log(4_000_000))))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        if rng.random() < 0.7:
+            g = inputs.rmat(int(np.ceil(np.log2(n))), 8, seed=1000 + i, n_vertices=n)
+            payloads.append(("d1", n, (pin(g.row_ptr), pin(g.col_idx)), g.nnz // 2))
+        else:
+            bp = inputs.bipartite(max(1, int(0.8 * n)), max(1, int(0.2 * n)), seed=2000 + i)
+            payloads.append(("pd2", bp.n_cols, (bp.n_rows, bp.n_cols, pin(bp.row_ptr),
+                                               pin(bp.col_idx), pin(bp.col_ptr), pin(bp.row_idx)),
+                             bp.nnz))
+    reqs = [(payloads[i % n_payloads], int(rng.integers(1, 1 << 40))) for i in range(n_requests)]
+    outs_plain = [np.zeros(p[1], dtype=np.int32) for p, _ in reqs]
+    outs_srv = [np.zeros(p[1], dtype=np.int32) for p, _ in reqs]
+
+    def plain_call(i):
+        (kind, n, a, _), sd = reqs[i]
+        if kind == "d1":
+            pgc.pgc_color_d1(a[0], a[1], seed=sd, colors=outs_plain[i])
+        else:
+            pgc.pgc_color_pd2(*a, seed=sd, colors=outs_plain[i])
+
+    for i in range(min(4, n_requests)):     # warm-up
+        plain_call(i)
+    # plain service time per request (FIFO capacity)
+    svc = []
+    for i in range(n_requests):
+        t0 = time.perf_counter()
+        plain_call(i)
+        svc.append(time.perf_counter() - t0)
+    cap = n_requests / sum(svc)
+    rate = load * cap
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    # FIFO of plain calls under the same arrivals (single worker)
+    t_free, lat_plain = 0.0, []
+    for a, sv in zip(arrivals, svc):
+        start = max(a, t_free)
+        t_free = start + sv
+        lat_plain.append(t_free - a)
+    # served: a producer submits at the arrival times, the caller waits
+    budget = 48 << 30
+    lat_srv = [0.0] * n_requests
+    with pgc.PgcServer(hbm_budget_bytes=budget, max_active=16) as srv:
+        for i in range(min(4, n_requests)):   # warm the slots' graphs
+            (kind, n, a, _), sd = reqs[i]
+            rid = (srv.submit_d1(a[0], a[1], seed=sd) if kind == "d1"
+                   else srv.submit_pd2(*a, seed=sd))
+            srv.wait(rid)
+        ids = [None] * n_requests
+        t_start = time.perf_counter()
+        t_sub = [0.0] * n_requests
+
+        def producer():
+            for i in range(n_requests):
+                delay = t_start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                (kind, n, a, _), sd = reqs[i]
+                t_sub[i] = time.perf_counter()
+                ids[i] = (srv.submit_d1(a[0], a[1], seed=sd, colors=outs_srv[i]) if kind == "d1"
+                          else srv.submit_pd2(*a, seed=sd, colors=outs_srv[i]))
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        for i in range(n_requests):
+            _, info = srv.wait(ids[i])
+            # steady-clock stamps share time.perf_counter's clock (CLOCK_MONOTONIC)
+            lat_srv[i] = info.t_done_ns * 1e-9 - (t_start + arrivals[i])
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+    same = all(np.array_equal(a, b) for a, b in zip(outs_plain, outs_srv))
+    edges = sum(p[3] for p, _ in reqs)
+    q = lambda v, x: float(np.percentile(v, x) * 1000)
+    return {"workload": f"{n_requests} requests over {n_payloads} payloads, 70% D1 / 30% PD2, "
+                        "n log-uniform [1K, 4M], Poisson arrivals",
+            "load": load, "rate_per_s": rate, "plain_capacity_per_s": cap,
+            "p50_ms": q(lat_srv, 50), "p99_ms": q(lat_srv, 99),
+            "plain_fifo_p50_ms": q(lat_plain, 50), "plain_fifo_p99_ms": q(lat_plain, 99),
+            "served_edges_per_s": edges / wall, "plain_edges_per_s": edges / sum(svc),
+            "max_active_seen": st["max_active_seen"], "peak_bytes": st["peak_bytes"],
+            "budget_bytes": budget, "identical_colors": bool(same)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +361,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-payloads", type=int, default=24)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--dump-profile", default=None,
                     help="write per-launch times and the per-round trace to this JSON file")
     args = ap.parse_args()
@@ -345,6 +498,15 @@ def main():
                          f"({sg.nnz} entries, 1/{2**(args.scale-args.cpu_baseline_scale)} of the "
                          f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
 
+    batch = serve = None
+    if rank == 0 and not args.no_batch:
+        batch = bench_batch(pgc, inputs, torch, dev, args.batch_graphs)
+        log("[batch]", json.dumps(batch))
+    if rank == 0 and not args.no_serve:
+        serve = bench_serve(pgc, inputs, torch, args.serve_requests, args.serve_payloads,
+                            args.serve_load)
+        log("[serve]", json.dumps(serve))
+
     if rank == 0:
         launches_per_step = 3 * rounds + 2  # classify, build, tier, then (assign,) detect, push
         out = {
@@ -359,6 +521,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((4 * (n + 1 + nnz)) / 1e9)},
             "nnz_per_s": value * 2, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+            "batched": batch, "served": serve,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
