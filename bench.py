@@ -255,7 +255,7 @@ def bench_batch(pgc, inputs, torch, dev, num_graphs):
             "max_rounds": int(gr.max().item()), "gen_s": gen_s, "autotuned": True}
 
 
-def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, seed=7):
+def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, slots, seed=7):
     """Served form vs a plain FIFO of single calls, same Poisson arrivals.
     Payloads (70% D1 R-MAT scale-matched, edge factor 8; 30% PD2 rows
     0.8n x columns 0.2n, rows 1 + Poisson(7); n log-uniform [1K, 4M]) are
@@ -276,8 +276,9 @@ def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, seed=7):
                                                pin(bp.col_idx), pin(bp.col_ptr), pin(bp.row_idx)),
                              bp.nnz))
     reqs = [(payloads[i % n_payloads], int(rng.integers(1, 1 << 40))) for i in range(n_requests)]
-    outs_plain = [np.zeros(p[1], dtype=np.int32) for p, _ in reqs]
-    outs_srv = [np.zeros(p[1], dtype=np.int32) for p, _ in reqs]
+    pinned = lambda k: torch.zeros(k, dtype=torch.int32).pin_memory().numpy()
+    outs_plain = [pinned(p[1]) for p, _ in reqs]
+    outs_srv = [pinned(p[1]) for p, _ in reqs]
 
     def plain_call(i):
         (kind, n, a, _), sd = reqs[i]
@@ -306,11 +307,15 @@ def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, seed=7):
     # served: a producer submits at the arrival times, the caller waits
     budget = 48 << 30
     lat_srv = [0.0] * n_requests
-    with pgc.PgcServer(hbm_budget_bytes=budget, max_active=16) as srv:
-        for i in range(min(4, n_requests)):   # warm the slots' graphs
+    with pgc.PgcServer(hbm_budget_bytes=budget, max_active=slots) as srv:
+        # warm every slot (graph instantiation, pinned staging) before timing
+        warm = [(i % n_requests) for i in range(2 * slots)]
+        wids = []
+        for i in warm:
             (kind, n, a, _), sd = reqs[i]
-            rid = (srv.submit_d1(a[0], a[1], seed=sd) if kind == "d1"
-                   else srv.submit_pd2(*a, seed=sd))
+            wids.append(srv.submit_d1(a[0], a[1], seed=sd) if kind == "d1"
+                        else srv.submit_pd2(*a, seed=sd))
+        for rid in wids:
             srv.wait(rid)
         ids = [None] * n_requests
         t_start = time.perf_counter()
@@ -344,6 +349,7 @@ def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, seed=7):
             "p50_ms": q(lat_srv, 50), "p99_ms": q(lat_srv, 99),
             "plain_fifo_p50_ms": q(lat_plain, 50), "plain_fifo_p99_ms": q(lat_plain, 99),
             "served_edges_per_s": edges / wall, "plain_edges_per_s": edges / sum(svc),
+            "slots": slots,
             "max_active_seen": st["max_active_seen"], "peak_bytes": st["peak_bytes"],
             "budget_bytes": budget, "identical_colors": bool(same)}
 
@@ -365,6 +371,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-payloads", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--loop", default="device", choices=["device", "host"],
+                    help="round loop of the timed steps: device-side CUDA graph (default) or "
+                         "host-driven launches (used for ncu, which cannot profile kernels "
+                         "inside conditional graphs)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--dump-profile", default=None,
@@ -405,8 +416,11 @@ def main():
     colors = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    step_flags = pgc.PGC_HOST_LOOP if args.loop == "host" else 0
+
     def step():
-        return pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream)
+        return pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
+                                flags=step_flags)
 
     res = None
     for _ in range(args.warmup):
@@ -504,7 +518,7 @@ def main():
         log("[batch]", json.dumps(batch))
     if rank == 0 and not args.no_serve:
         serve = bench_serve(pgc, inputs, torch, args.serve_requests, args.serve_payloads,
-                            args.serve_load)
+                            args.serve_load, args.serve_slots)
         log("[serve]", json.dumps(serve))
 
     if rank == 0:

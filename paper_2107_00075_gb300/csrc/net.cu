@@ -925,6 +925,10 @@ pgc_status slot_launch_pd2(void* c, void* scratch, int n_rows, int n_cols, const
     return launch_known(*cx, scratch, in, windows, seed, o, stream);
 }
 
+bool slot_overflowed(void* c) {
+    return static_cast<Context*>(c)->h_state.as<State>()->status == ST_OVERFLOW;
+}
+
 pgc_status slot_finish(void* c, int* rounds, int* num_colors) {
     return finish_known(*static_cast<Context*>(c), rounds, num_colors);
 }

@@ -83,6 +83,7 @@ pgc_status slot_launch_pd2(void* slot, void* scratch, int n_rows, int n_cols, co
                            const int* col_idx, const int* col_ptr, const int* row_idx, int* colors,
                            int windows, uint64_t seed, cudaStream_t stream);
 pgc_status slot_finish(void* slot, int* rounds, int* num_colors);
+bool slot_overflowed(void* slot);   // the last launch needed more mask windows
 }  // namespace net
 
 }  // namespace pgc

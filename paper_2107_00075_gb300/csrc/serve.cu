@@ -80,6 +80,11 @@ class Arena {
 
 enum Kind { KIND_D1 = 1, KIND_PD2 = 3 };
 
+// PD2 requests first run with masks for colors 1..128; a request that needs
+// more is re-queued at the head with the window count of its exact color
+// bound (the run is deterministic, so the retry gives the same colors).
+constexpr int kFirstWindows = 2;
+
 struct Request {
     long long id = 0;
     int kind = KIND_D1;
@@ -87,7 +92,8 @@ struct Request {
     long long nnz = 0;
     const int *rp = nullptr, *ci = nullptr, *cp = nullptr, *ri = nullptr;
     int* out = nullptr;
-    bool out_on_device = false;
+    bool out_on_device = false;   // device memory: copied device to device
+    bool out_pinned = false;      // pinned host memory: copied directly
     uint64_t seed = 1;
     int windows = 1;
     size_t bytes = 0, off = 0;
@@ -97,6 +103,21 @@ struct Request {
     int rounds = 0, num_colors = 0;
     long long t_submit = 0, t_admit = 0, t_done = 0;
 };
+
+// max over columns v of sum over v's rows of (row length - 1): a first-fit
+// color never exceeds this + 1.
+static int pd2_windows(const Request& r) {
+    long long bound = 0;
+    for (int v = 0; v < r.n_cols; ++v) {
+        long long b = 0;
+        for (int e = r.cp[v]; e < r.cp[v + 1]; ++e) {
+            const int row = r.ri[e];
+            b += r.rp[row + 1] - r.rp[row] - 1;
+        }
+        bound = std::max(bound, b);
+    }
+    return (int)std::max<long long>(1, std::min<long long>(64, (bound + 1 + 63) / 64));
+}
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -177,8 +198,8 @@ static pgc_status start(Server& S, Slot& sl, Request& r) {
                                                 d_ri, d_col, r.windows, r.seed, st))
             return s;
     }
-    if (r.out_on_device) {
-        PGC_CUDA(cudaMemcpyAsync(r.out, d_col, (size_t)r.n * 4, cudaMemcpyDeviceToDevice, st));
+    if (r.out_on_device || r.out_pinned) {
+        PGC_CUDA(cudaMemcpyAsync(r.out, d_col, (size_t)r.n * 4, cudaMemcpyDefault, st));
     } else {
         if (pgc_status s = sl.colors.ensure((size_t)r.n * 4)) return s;
         PGC_CUDA(cudaMemcpyAsync(sl.colors.ptr, d_col, (size_t)r.n * 4, cudaMemcpyDeviceToHost, st));
@@ -198,7 +219,29 @@ static void complete(Server& S, Slot& sl, pgc_status launch_status) {
         s = r.kind == KIND_D1 ? sl.d1e.finish(Opts(), &r.rounds, &r.num_colors)
                               : net::slot_finish(sl.nete, &r.rounds, &r.num_colors);
     }
-    if (s == PGC_OK && !r.out_on_device) std::memcpy(r.out, sl.colors.ptr, (size_t)r.n * 4);
+    if (s == PGC_ERR_NO_CONVERGE && r.kind == KIND_PD2 && r.windows == kFirstWindows &&
+        net::slot_overflowed(sl.nete)) {
+        // more than 128 colors: retry with masks sized by the exact bound
+        const int w = pd2_windows(r);
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.arena.release(r.off, r.bytes);
+        sl.req = nullptr;
+        S.active -= 1;
+        r.windows = std::max(w, kFirstWindows + 1);
+        r.bytes = footprint(r);
+        if (r.bytes > S.budget) {
+            r.status = fail(PGC_ERR_BUSY, "request footprint exceeds the server's HBM budget");
+            r.done = true;
+            r.t_done = now_ns();
+            S.completed += 1;
+            S.cv_done.notify_all();
+        } else {
+            S.queue.push_front(&r);
+        }
+        return;
+    }
+    if (s == PGC_OK && !r.out_on_device && !r.out_pinned)
+        std::memcpy(r.out, sl.colors.ptr, (size_t)r.n * 4);
     std::lock_guard<std::mutex> lk(S.mu);
     r.status = s;
     r.done = true;
@@ -295,6 +338,17 @@ static pgc_status submit(Server* S, Request* r, long long* req_id) {
     return PGC_OK;
 }
 
+static void classify_output(Request* r, int* colors) {
+    r->out = colors;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, colors) != cudaSuccess) {
+        cudaGetLastError();
+        a.type = cudaMemoryTypeUnregistered;
+    }
+    r->out_on_device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    r->out_pinned = a.type == cudaMemoryTypeHost;
+}
+
 static void fill_info(const Request& r, pgc_request_info* info) {
     if (!info) return;
     info->status = r.status;
@@ -375,8 +429,7 @@ pgc_status pgc_server_submit_d1(pgc_server* srv, int32_t n, const int32_t* row_p
     r->nnz = nnz;
     r->rp = row_ptr;
     r->ci = col_idx;
-    r->out = colors;
-    r->out_on_device = !pgc::is_host_pointer(colors);
+    pgc::serve::classify_output(r, colors);
     r->seed = seed;
     long long id = 0;
     pgc_status s = pgc::serve::submit(&srv->impl, r, &id);
@@ -395,16 +448,6 @@ pgc_status pgc_server_submit_pd2(pgc_server* srv, int32_t n_rows, int32_t n_cols
         return pgc::fail(PGC_ERR_INVALID_ARG, "server PD2 inputs must be host memory");
     const long long nnz = row_ptr[n_rows];
     if (nnz != col_ptr[n_cols] || nnz < 0) return pgc::fail(PGC_ERR_INVALID_ARG, "CSR/CSC mismatch");
-    // mask windows from the color bound, computed here on the host
-    long long bound = 0;
-    for (int v = 0; v < n_cols; ++v) {
-        long long b = 0;
-        for (int e = col_ptr[v]; e < col_ptr[v + 1]; ++e) {
-            const int r = row_idx[e];
-            b += row_ptr[r + 1] - row_ptr[r] - 1;
-        }
-        bound = std::max(bound, b);
-    }
     auto* r = new Request();
     r->kind = pgc::serve::KIND_PD2;
     r->n = n_cols;
@@ -415,10 +458,9 @@ pgc_status pgc_server_submit_pd2(pgc_server* srv, int32_t n_rows, int32_t n_cols
     r->ci = col_idx;
     r->cp = col_ptr;
     r->ri = row_idx;
-    r->out = colors;
-    r->out_on_device = !pgc::is_host_pointer(colors);
+    pgc::serve::classify_output(r, colors);
     r->seed = seed;
-    r->windows = (int)std::max<long long>(1, std::min<long long>(64, (bound + 1 + 63) / 64));
+    r->windows = pgc::serve::kFirstWindows;
     long long id = 0;
     pgc_status s = pgc::serve::submit(&srv->impl, r, &id);
     *req_id = id;

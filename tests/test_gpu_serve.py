@@ -126,3 +126,18 @@ def test_poll_timeout_unknown_and_device_outputs(pgc):
             srv.wait(rid)
         assert e.value.status == 7
     assert torch.equal(out.cpu(), torch.from_numpy(alone(pgc, "d1", g, 5)[0]))
+
+
+def test_pd2_needing_more_than_128_colors_is_retried(pgc):
+    """A PD2 request whose coloring needs more colors than the first mask
+    size is re-run transparently with larger masks."""
+    from tests import _graphs
+    rows = [list(range(200))] + [[i, (i + 7) % 200] for i in range(50)]
+    b = _graphs.bipartite_from_rows(rows, 200)
+    with pgc.PgcServer(hbm_budget_bytes=64 << 20, max_active=2) as srv:
+        rid = srv.submit_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                             seed=3)
+        colors, info = srv.wait(rid)
+    want = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                            seed=3)
+    assert info.num_colors == 200 and np.array_equal(colors, want.colors)
