@@ -100,13 +100,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # algorithmic bytes (per kernel, from the per-round trace)
 # --------------------------------------------------------------------------
-def d1_algorithmic_bytes(trace_w, trace_h, n, nnz, deg):
+def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None):
     """Bytes each kernel must move for one coloring (int32 ids and colors,
-    64-bit forbidden-color words), from |W_r| and H_r = sum over W_r of
-    |H(v)| (the per-round scan lists):
-      classify: offsets 4(n+1) + degree, color, list-length and two flag
-                writes 20n + forbidden word 8n + overflow bitmap clear
-                4 sum(deg/32 + 1 | deg >= 64) + worklist 4n
+    64-bit forbidden-color words), from the per-round trace: |W_r|,
+    S_r = sum of deg over W_r and H_r = sum of |H(v)| over W_r (the scan
+    lists).  Rounds from tail_at on run inside the cooperative tail kernel.
+      classify: offsets 4(n+1) + degree, color, list-length writes 12n +
+                forbidden word 8n + worklist 4n (overflow-bitmap clears of
+                vertices with deg >= 64 not counted)
       build:    worklist 4n + offsets 8n + adjacency 4 nnz + neighbor degree
                 4 nnz + H lists 4 H_1 + list lengths 4n
       tier:     list lengths 4n + worklists 4n
@@ -114,22 +115,31 @@ def d1_algorithmic_bytes(trace_w, trace_h, n, nnz, deg):
       detect:   worklist, offset, list length, own color, commit/append:
                 20 |W_r| + H entries and their colors 8 H_r (upper bound: a
                 loser stops at its first conflict)
-      push:     per adjacency entry of a vertex of degree > 32: neighbor id 4 +
-                forbidden-word update 8 = 12 B
+      push:     per adjacency entry of the round's winners (S_r - S_{r+1},
+                whether pushed inline by detect or by the push kernel):
+                neighbor id 4 + forbidden-word update 8 = 12 B
     """
     w = np.asarray(trace_w, dtype=np.float64)
+    sw = np.asarray(trace_s, dtype=np.float64)
     hh = np.asarray(trace_h, dtype=np.float64)
-    deg = np.asarray(deg)
-    big = float(deg[deg > 32].sum())
-    ovf = float(((deg[deg >= 64] >> 5) + 1).sum())
-    return {
-        "d1_classify": 4.0 * (n + 1) + 32.0 * n + 4.0 * ovf,
+    R = len(w)
+    t = R if tail_at is None else tail_at
+    won = sw - np.append(sw[1:], 0.0)
+    asg = 16 * w
+    asg[0] = 0.0
+    det = 20 * w + 8 * hh
+    psh = 12 * won
+    out = {
+        "d1_classify": 4.0 * (n + 1) + 24.0 * n,
         "d1_build": 16.0 * n + 8.0 * nnz + 4.0 * float(hh[0]),
         "d1_tier": 8.0 * n,
-        "d1_assign": float(np.sum(16 * w[1:])),
-        "d1_detect": float(np.sum(20 * w + 8 * hh)),
-        "d1_push": 12.0 * big,
+        "d1_assign": float(asg[:t].sum()),
+        "d1_detect": float(det[:t].sum()),
+        "d1_push": float(psh[:t].sum()),
     }
+    if t < R:
+        out["d1_tail"] = float(asg[t:].sum() + det[t:].sum() + psh[t:].sum())
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -376,6 +386,11 @@ def main():
                     help="round loop of the timed steps: device-side CUDA graph (default) or "
                          "host-driven launches (used for ncu, which cannot profile kernels "
                          "inside conditional graphs)")
+    ap.add_argument("--tail-vertices", type=int, default=0,
+                    help="worklist size below which the remaining rounds run in one "
+                         "cooperative launch (0: library default, < 0: never)")
+    ap.add_argument("--timeout-ms", type=int, default=0,
+                    help="device round-loop budget (raise it for runs under a profiler)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--dump-profile", default=None,
@@ -420,7 +435,8 @@ def main():
 
     def step():
         return pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
-                                flags=step_flags)
+                                flags=step_flags, tail_vertices=args.tail_vertices,
+                                timeout_ms=args.timeout_ms)
 
     res = None
     for _ in range(args.warmup):
@@ -473,16 +489,24 @@ def main():
     # ---- roofline of the dominant kernel (host-loop mode, CUDA events) ----
     roofline = None
     kernels = {}
+    trace_w = None
     peak, peak_kind = load_peaks()
     if not args.no_profile:
         prof = pgc.Profile(trace_cap=1 << 16, launch_cap=1 << 18)
         pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
-                         flags=pgc.PGC_HOST_LOOP, profile=prof)
+                         flags=pgc.PGC_HOST_LOOP, profile=prof,
+                         tail_vertices=args.tail_vertices, timeout_ms=args.timeout_ms)
         if args.dump_profile:
             json.dump({"launches": prof.launches, "trace_w": prof.trace_w.tolist(),
                        "trace_s": prof.trace_s.tolist(), "trace_h": prof.trace_h.tolist()},
                       open(args.dump_profile, "w"))
-        nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_h, n, nnz, np.diff(g.row_ptr))
+        trace_w = prof.trace_w
+        tail_w = 65536 if args.tail_vertices == 0 else args.tail_vertices
+        tail_at = None
+        if tail_w > 0:
+            tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
+        nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, n, nnz,
+                                      tail_at)
         for name, kms in prof.kernel_ms.items():
             kernels[name] = {"ms": kms, "launches": prof.kernel_launches[name],
                              "alg_bytes": nbytes.get(name)}
@@ -522,7 +546,14 @@ def main():
         log("[serve]", json.dumps(serve))
 
     if rank == 0:
-        launches_per_step = 3 * rounds + 2  # classify, build, tier, then (assign,) detect, push
+        # classify, build, tier, then (assign,) detect, push per round until the
+        # worklist is small, then one cooperative tail launch
+        tail_w = 65536 if args.tail_vertices == 0 else args.tail_vertices
+        tail_at = None
+        if trace_w is not None and tail_w > 0:
+            tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
+        loop_rounds = tail_at if tail_at is not None else rounds
+        launches_per_step = 3 + 3 * loop_rounds - 1 + (1 if tail_at is not None else 0)
         out = {
             "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

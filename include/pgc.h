@@ -115,7 +115,10 @@ typedef struct {
     int32_t block;             /* 0 => default threads per block (128..1024) */
     int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
     int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */
-    int32_t reserved;
+    int32_t tail_vertices;     /* D1: once the worklist has at most this many
+                                  vertices, the remaining rounds run in one
+                                  cooperative launch with grid barriers;
+                                  0 => 65536, < 0 => never */
     pgc_profile *profile;      /* nullable */
 } pgc_opts;
 

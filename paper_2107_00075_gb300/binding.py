@@ -48,7 +48,7 @@ class PgcOptsC(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("max_rounds", ctypes.c_int32),
                 ("mid_degree", ctypes.c_int32), ("hub_degree", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
-                ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int32), ("tail_vertices", ctypes.c_int32),
                 ("profile", ctypes.POINTER(PgcProfileC))]
 
 
@@ -175,9 +175,10 @@ def _stream_handle(stream, device):
 
 
 def _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm, timeout_ms,
-               profile: Optional[Profile]):
+               profile: Optional[Profile], tail_vertices: int = 0):
     o = PgcOptsC()
     lib().pgc_opts_init(ctypes.byref(o))
+    o.tail_vertices = tail_vertices
     o.flags, o.max_rounds = flags, max_rounds
     o.mid_degree, o.hub_degree = mid_degree, hub_degree
     o.block, o.grid_per_sm, o.timeout_ms = block, grid_per_sm, timeout_ms
@@ -240,10 +241,12 @@ def _device_ctx(device):
 def pgc_color_d1(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0,
                  max_rounds: int = 0, mid_degree: int = 0, hub_degree: int = 0,
                  block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
-                 profile: Optional[Profile] = None, stream=None) -> ColorResult:
+                 tail_vertices: int = 0, profile: Optional[Profile] = None,
+                 stream=None) -> ColorResult:
     """Distance-1 coloring of a symmetric int32 CSR graph (see pgc.h)."""
     return _color_sym("pgc_color_d1", row_ptr, col_idx, seed, colors, flags, max_rounds,
-                      mid_degree, hub_degree, block, grid_per_sm, timeout_ms, profile, stream)
+                      mid_degree, hub_degree, block, grid_per_sm, timeout_ms, profile, stream,
+                      tail_vertices)
 
 
 def pgc_color_d2(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0,
@@ -284,7 +287,7 @@ def pgc_color_pd2(n_rows: int, n_cols: int, row_ptr, col_idx, col_ptr, row_idx,
 
 
 def _color_sym(fname, row_ptr, col_idx, seed, colors, flags, max_rounds, mid_degree,
-               hub_degree, block, grid_per_sm, timeout_ms, profile, stream):
+               hub_degree, block, grid_per_sm, timeout_ms, profile, stream, tail_vertices=0):
     rp = _Arr(row_ptr, "row_ptr")
     ci = _Arr(col_idx, "col_idx")
     n = rp.n - 1
@@ -296,7 +299,7 @@ def _color_sym(fname, row_ptr, col_idx, seed, colors, flags, max_rounds, mid_deg
     if co.n < n:
         raise ValueError("colors is shorter than n")
     o, keep = _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm,
-                         timeout_ms, profile)
+                         timeout_ms, profile, tail_vertices)
     rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
     dev = rp.device or co.device
     with _device_ctx(dev):
@@ -337,7 +340,8 @@ def pgc_color_d1_batch(vtx_off, nnz_off, row_ptr, col_idx, seed: int = 1, colors
                        rounds_per_graph=None, colors_per_graph=None, *, flags: int = 0,
                        max_rounds: int = 0, mid_degree: int = 0, hub_degree: int = 0,
                        block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
-                       profile: Optional[Profile] = None, stream=None) -> BatchResult:
+                       tail_vertices: int = 0, profile: Optional[Profile] = None,
+                       stream=None) -> BatchResult:
     """Batched distance-1 coloring of independent graphs (see pgc.h)."""
     vo, no = _Arr64(vtx_off, "vtx_off"), _Arr64(nnz_off, "nnz_off")
     rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
@@ -355,7 +359,7 @@ def pgc_color_d1_batch(vtx_off, nnz_off, row_ptr, col_idx, seed: int = 1, colors
     co = _Arr(colors, "colors")
     gr, gc = _Arr(rounds_per_graph, "rounds_per_graph"), _Arr(colors_per_graph, "colors_per_graph")
     o, keep = _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm,
-                         timeout_ms, profile)
+                         timeout_ms, profile, tail_vertices)
     rounds = ctypes.c_int32(0)
     with _device_ctx(dev):
         st = lib().pgc_color_d1_batch(G, vo.ptr, no.ptr, rp.ptr, ci.ptr if ci.n else None,

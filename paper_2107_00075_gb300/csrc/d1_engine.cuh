@@ -105,7 +105,7 @@ constexpr int kBuildItem = 512; // setup: adjacency items of this length
 constexpr int kPushItem = 128;  // push: adjacency items of this length
 constexpr int kInlinePush = 32; // S-tier winners up to this degree push inline
 
-enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3 };
+enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3, ST_BARRIER = 4 };
 
 struct State {
     int round;        // round being executed (1-based)
@@ -119,6 +119,10 @@ struct State {
     int push_cnt;     // push work items queued this round
     unsigned blocks_done;
     unsigned l_next;  // dynamic index into the L-tier worklist
+    int tail;         // 1: the graph loop handed the remaining rounds to d1_tail
+    unsigned bar_count;         // d1_tail grid barrier: arrivals
+    unsigned bar_gen;           // d1_tail grid barrier: generation
+    int bar_timeout;            // d1_tail: a barrier wait gave up
     unsigned long long s_next;  // sum of degrees of the next worklist
     unsigned long long h_next;  // sum of |H(v)| over the next worklist
     unsigned long long h_first; // sum of |H(v)| over all vertices
@@ -154,6 +158,7 @@ struct Problem {
     int max_rounds;
     int det_s;
     int det_m;
+    int tail_w;        // hand over to d1_tail once the worklist is this small (0: never)
 };
 
 // key(u) > key(v) for u, v of the same graph (hash of graph-local ids),
@@ -401,16 +406,8 @@ __device__ __forceinline__ void assign_one(const Problem<V>& P, int v) {
 }
 
 template <class V>
-__global__ void d1_assign(const Problem<V>* __restrict__ Pp, cudaGraphConditionalHandle h,
-                          int use_cond) {
-    const Problem<V>& P = *Pp;
+__device__ __forceinline__ void assign_phase(const Problem<V>& P) {
     State* st = P.st;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // The loop continues only if this round's detect says so: should its
-        // round control ever not run, the device loop ends instead of spinning.
-        if (use_cond) cudaGraphSetConditional(h, 0u);
-        st->push_cnt = 0;   // the previous round's push kernel has finished
-    }
     const int cp = *(volatile int*)&st->round & 1;
     const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nl[cp];
     const long long total = (long long)n0 + n1 + n2;
@@ -422,11 +419,26 @@ __global__ void d1_assign(const Problem<V>* __restrict__ Pp, cudaGraphConditiona
     }
 }
 
+template <class V>
+__global__ void d1_assign(const Problem<V>* __restrict__ Pp, cudaGraphConditionalHandle h,
+                          int use_cond) {
+    const Problem<V>& P = *Pp;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // The loop continues only if this round's detect says so: should its
+        // round control ever not run, the device loop ends instead of spinning.
+        if (use_cond) cudaGraphSetConditional(h, 0u);
+        P.st->push_cnt = 0;   // the previous round's push kernel has finished
+    }
+    assign_phase(P);
+}
+
 // ---------------------------------------------------------------------------
 // detect + commit + compact + inline push (+ round control in the last block)
 // ---------------------------------------------------------------------------
+// End of round r: record the trace, decide whether to go on, set up round
+// r+1.  Returns 1 when the coloring is finished (or has failed).
 template <class V>
-__device__ void round_control(const Problem<V>& P, cudaGraphConditionalHandle h, int use_cond) {
+__device__ int round_decide(const Problem<V>& P) {
     State* st = P.st;
     const int r = st->round;
     const int cp = r & 1, np = cp ^ 1;
@@ -462,8 +474,18 @@ __device__ void round_control(const Problem<V>& P, cudaGraphConditionalHandle h,
     st->done = done;
     st->blocks_done = 0u;
     st->l_next = 0u;
+    st->tail = (!done && nxt <= P.tail_w) ? 1 : 0;
     __threadfence();
-    if (use_cond) cudaGraphSetConditional(h, done ? 0u : 1u);
+    return done;
+}
+
+// Round control of the launch-per-round loop: the WHILE node repeats while
+// the coloring is unfinished and the worklist is larger than tail_w; the
+// remaining rounds go to d1_tail.
+template <class V>
+__device__ void round_control(const Problem<V>& P, cudaGraphConditionalHandle h, int use_cond) {
+    const int done = round_decide(P);
+    if (use_cond) cudaGraphSetConditional(h, (done || P.st->tail) ? 0u : 1u);
 }
 
 // Queue the push of v's color: ceil(deg / kPushItem) work items.
@@ -490,11 +512,10 @@ __device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg
     return false;
 }
 
+// Detection, commit, compaction and inline push for one round (every block
+// of the grid takes part).
 template <class V>
-__global__ void d1_detect(const Problem<V>* __restrict__ Pp, cudaGraphConditionalHandle h,
-                          int use_cond) {
-    extern __shared__ int smem[];
-    const Problem<V>& P = *Pp;
+__device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     State* st = P.st;
     const int r = *(volatile int*)&st->round;
     const int cp = r & 1, np = cp ^ 1;
@@ -639,6 +660,16 @@ __global__ void d1_detect(const Problem<V>* __restrict__ Pp, cudaGraphConditiona
         if (my_h > 0) atomicAdd(&st->h_next, my_h);
     }
 
+}
+
+template <class V>
+__global__ void __maxnreg__(40) d1_detect(const Problem<V>* __restrict__ Pp,
+                                          cudaGraphConditionalHandle h, int use_cond) {
+    extern __shared__ int smem[];
+    const Problem<V>& P = *Pp;
+    State* st = P.st;
+    detect_phase(P, smem);
+
     // --- last block runs the round control ---
     __shared__ int s_last;
     __threadfence();
@@ -658,8 +689,7 @@ __global__ void d1_detect(const Problem<V>* __restrict__ Pp, cudaGraphConditiona
 // push: winners' colors into the forbidden sets of their neighbors
 // ---------------------------------------------------------------------------
 template <class V>
-__global__ void d1_push(const Problem<V>* __restrict__ Pp) {
-    const Problem<V>& P = *Pp;
+__device__ __forceinline__ void push_phase(const Problem<V>& P) {
     const int nq = *(volatile int*)&P.st->push_cnt;
     const int lane = lane_id(), wpb = blockDim.x >> 5;
     for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < nq; q += gridDim.x * wpb) {
@@ -682,6 +712,77 @@ __global__ void d1_push(const Problem<V>* __restrict__ Pp) {
             for (int j = 0; j < 4; ++j)
                 if (u[j] >= 0 && u[j] != v) push_color(P, u[j], g, c);
         }
+    }
+}
+
+template <class V>
+__global__ void d1_push(const Problem<V>* __restrict__ Pp) {
+    push_phase(*Pp);
+}
+
+// ---------------------------------------------------------------------------
+// tail: the last, small rounds in one cooperative launch
+// ---------------------------------------------------------------------------
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  A
+// wait that exceeds ~2^22 polls (about a second) gives up, records the
+// failure and lets the kernel return with an error instead of hanging.
+__device__ __forceinline__ bool grid_barrier(State* st) {
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = *(volatile unsigned*)&st->bar_gen;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            st->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            unsigned polls = 0;
+            while (*(volatile unsigned*)&st->bar_gen == gen) {
+                __nanosleep(128);
+                if (++polls > (1u << 22) || *(volatile int*)&st->bar_timeout) {
+                    atomicExch(&st->bar_timeout, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Runs assign / detect / push for every remaining round, with grid
+// barriers between the phases instead of kernel boundaries.  Entered when
+// the launch-per-round loop stopped with st->tail set; returns at once if
+// the coloring is already finished.
+template <class V>
+__global__ void __maxnreg__(40) d1_tail(const Problem<V>* __restrict__ Pp) {
+    extern __shared__ int smem[];
+    const Problem<V>& P = *Pp;
+    State* st = P.st;
+    if (*(volatile int*)&st->done || !*(volatile int*)&st->tail) return;
+    for (;;) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->push_cnt = 0;
+        assign_phase(P);
+        if (!grid_barrier(st)) break;
+        detect_phase(P, smem);
+        if (!grid_barrier(st)) break;
+        __shared__ int s_done;
+        if (blockIdx.x == 0 && threadIdx.x == 0) round_decide(P);
+        push_phase(P);
+        if (!grid_barrier(st)) break;
+        if (threadIdx.x == 0) s_done = *(volatile int*)&st->done;
+        __syncthreads();
+        if (s_done) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&st->bar_timeout) {
+        st->status = ST_BARRIER;
+        st->done = 1;
     }
 }
 
@@ -776,6 +877,7 @@ struct Engine {
     struct Geometry {
         int grid, block;
         size_t smem;   // two warp appenders per warp
+        int tail_grid; // co-resident blocks for the cooperative tail kernel
     };
 
     pgc_status geometry(const Opts& o, Geometry* g) {
@@ -789,6 +891,9 @@ struct Engine {
             per_sm = std::max(1, std::min(a, b));
         }
         g->grid = dev.num_sms * per_sm;
+        int t = 0;
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t, d1_tail<V>, o.block, g->smem));
+        g->tail_grid = dev.num_sms * std::max(1, std::min(t, std::max(per_sm, 1)));
         return PGC_OK;
     }
 
@@ -841,6 +946,14 @@ struct Engine {
         PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
         PGC_CUDA(cudaGraphAddKernelNode(&b_det, body, &b_asg, 1, &k_det));
         PGC_CUDA(cudaGraphAddKernelNode(&b_push, body, &b_det, 1, &k_push));
+        // the remaining small rounds: one cooperative launch
+        cudaKernelNodeParams k_tail = knode((void*)d1_tail<V>, g, g.smem, p_args);
+        k_tail.gridDim = dim3(g.tail_grid);
+        cudaGraphNode_t n_tail;
+        PGC_CUDA(cudaGraphAddKernelNode(&n_tail, graph, &n_loop, 1, &k_tail));
+        cudaLaunchAttributeValue coop = {};
+        coop.cooperative = 1;
+        PGC_CUDA(cudaGraphKernelNodeSetAttribute(n_tail, cudaLaunchAttributeCooperative, &coop));
         PGC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         g_grid = g.grid;
         g_block = g.block;
@@ -937,6 +1050,7 @@ struct Engine {
         hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
         hp->det_s = o.mid_degree;
         hp->det_m = o.hub_degree;
+        hp->tail_w = o.tail_vertices;
         PGC_CUDA(cudaMemcpyAsync(problem.ptr, hp, sizeof(Problem<V>), cudaMemcpyHostToDevice,
                                  stream));
         Problem<V>* dP = problem.as<Problem<V>>();
@@ -974,6 +1088,14 @@ struct Engine {
                                          stream));
                 PGC_CUDA(cudaStreamSynchronize(stream));
                 if (hs->done) break;
+                if (hs->tail) {   // the remaining rounds in one cooperative launch
+                    if (pgc_status s_ = kt.begin(6, "d1_tail")) return s_;
+                    void* args[] = {&dP};
+                    PGC_CUDA(cudaLaunchCooperativeKernel((void*)d1_tail<V>, dim3(g.tail_grid),
+                                                         dim3(g.block), args, g.smem, stream));
+                    if (pgc_status s_ = kt.end()) return s_;
+                    break;
+                }
                 if (round > hp->max_rounds + 1)
                     return fail(PGC_ERR_CUDA, "device round control did not finish the loop");
             }
@@ -1011,6 +1133,8 @@ struct Engine {
                 return fail(PGC_ERR_NO_CONVERGE, "a round committed no vertex (input not symmetric?)");
             case ST_MAX_ROUNDS: return fail(PGC_ERR_NO_CONVERGE, "max_rounds reached");
             case ST_TIMEOUT: return fail(PGC_ERR_TIMEOUT, "device round loop exceeded timeout_ms");
+            case ST_BARRIER:
+                return fail(PGC_ERR_TIMEOUT, "a grid barrier of the tail kernel timed out");
             default: return fail(PGC_ERR_CUDA, "unexpected device status");
         }
     }

@@ -94,6 +94,8 @@ pgc_status read_opts(const pgc_opts* in, Opts* out) {
         o.grid_per_sm = in->grid_per_sm;
         if (in->timeout_ms < 0) return fail(PGC_ERR_INVALID_ARG, "timeout_ms < 0");
         if (in->timeout_ms > 0) o.timeout_ms = in->timeout_ms;
+        if (in->tail_vertices > 0) o.tail_vertices = in->tail_vertices;
+        if (in->tail_vertices < 0) o.tail_vertices = 0;
         o.profile = in->profile;
     }
     if (o.hub_degree < o.mid_degree) o.hub_degree = o.mid_degree;

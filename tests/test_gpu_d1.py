@@ -171,3 +171,13 @@ def test_repeatable_and_stream(pgc):
         with torch.cuda.stream(s):
             outs.append(pgc.pgc_color_d1(rp, ci, seed=8, stream=s).colors.cpu().numpy())
     assert all(np.array_equal(outs[0], o) for o in outs)
+
+
+@pytest.mark.parametrize("tail", [-1, 1, 100, 5000, 1 << 30])
+def test_tail_kernel_threshold_does_not_change_colors(pgc, tail):
+    """The last rounds run in one cooperative launch once the worklist is
+    small; where the hand-over happens must not change anything."""
+    g = gen.rmat(14, 16, seed=11)
+    assert_parity(pgc, g, seed=3, tail_vertices=tail)
+    assert_parity(pgc, g, seed=3, tail_vertices=tail, flags=pgc.PGC_HOST_LOOP)
+    assert_parity(pgc, gen.stencil3d(16, 16, 16, points=7), seed=2, tail_vertices=tail)
