@@ -364,6 +364,48 @@ def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, slots, seed=7)
             "budget_bytes": budget, "identical_colors": bool(same)}
 
 
+def bench_net(pgc, inputs, torch, dev, reps=5):
+    """Distance-2 on the 27-point stencil 128^3 and partial distance-2 on the
+    4M x 1M pattern (config 3), inputs resident; edges = nnz/2 for D2 (a
+    symmetric graph) and nnz for PD2 (row-column entries)."""
+    out = {}
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g = inputs.stencil3d(128, 128, 128, points=27)
+    rp, ci = t(g.row_ptr), t(g.col_idx)
+    col = torch.empty(g.n, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(reps):
+        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / reps
+    out["d2_stencil27_128"] = {"n": g.n, "nnz": g.nnz, "ms": ms, "rounds": r.rounds,
+                               "num_colors": r.num_colors,
+                               "edges_per_s": (g.nnz / 2) / (ms / 1000)}
+    del rp, ci, col
+    b = inputs.bipartite(1 << 22, 1 << 20, seed=SEED)
+    a = [t(x) for x in (b.row_ptr, b.col_idx, b.col_ptr, b.row_idx)]
+    col = torch.empty(b.n_cols, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(reps):
+        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / reps
+    out["pd2_4Mx1M"] = {"rows": b.n_rows, "cols": b.n_cols, "nnz": b.nnz, "ms": ms,
+                        "rounds": r.rounds, "num_colors": r.num_colors,
+                        "edges_per_s": b.nnz / (ms / 1000)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,6 +434,7 @@ def main():
     ap.add_argument("--timeout-ms", type=int, default=0,
                     help="device round-loop budget (raise it for runs under a profiler)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--dump-profile", default=None,
                     help="write per-launch times and the per-round trace to this JSON file")
@@ -501,7 +544,7 @@ def main():
                        "trace_s": prof.trace_s.tolist(), "trace_h": prof.trace_h.tolist()},
                       open(args.dump_profile, "w"))
         trace_w = prof.trace_w
-        tail_w = 65536 if args.tail_vertices == 0 else args.tail_vertices
+        tail_w = 4096 if args.tail_vertices == 0 else args.tail_vertices
         tail_at = None
         if tail_w > 0:
             tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
@@ -536,7 +579,10 @@ def main():
                          f"({sg.nnz} entries, 1/{2**(args.scale-args.cpu_baseline_scale)} of the "
                          f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
 
-    batch = serve = None
+    batch = serve = net = None
+    if rank == 0 and not args.no_net:
+        net = bench_net(pgc, inputs, torch, dev)
+        log("[net]", json.dumps(net))
     if rank == 0 and not args.no_batch:
         batch = bench_batch(pgc, inputs, torch, dev, args.batch_graphs)
         log("[batch]", json.dumps(batch))
@@ -548,7 +594,7 @@ def main():
     if rank == 0:
         # classify, build, tier, then (assign,) detect, push per round until the
         # worklist is small, then one cooperative tail launch
-        tail_w = 65536 if args.tail_vertices == 0 else args.tail_vertices
+        tail_w = 4096 if args.tail_vertices == 0 else args.tail_vertices
         tail_at = None
         if trace_w is not None and tail_w > 0:
             tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
@@ -566,7 +612,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((4 * (n + 1 + nnz)) / 1e9)},
             "nnz_per_s": value * 2, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
-            "batched": batch, "served": serve,
+            "batched": batch, "served": serve, "distance2": net,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -118,7 +118,7 @@ typedef struct {
     int32_t tail_vertices;     /* D1: once the worklist has at most this many
                                   vertices, the remaining rounds run in one
                                   cooperative launch with grid barriers;
-                                  0 => 65536, < 0 => never */
+                                  0 => 4096, < 0 => never */
     pgc_profile *profile;      /* nullable */
 } pgc_opts;
 

@@ -258,7 +258,7 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
 // setup 2: H(v) = neighbors with higher priority, stored at v's row start
 // ---------------------------------------------------------------------------
 template <class V>
-__global__ void d1_build(const Problem<V>* __restrict__ Pp) {
+__global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
     const Problem<V>& P = *Pp;
     State* st = P.st;
     const int* __restrict__ dg = P.deg;

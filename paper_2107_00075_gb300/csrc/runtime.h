@@ -52,7 +52,7 @@ struct Opts {
     int32_t block = 256;
     int32_t grid_per_sm = 0;
     int32_t timeout_ms = 60000;
-    int32_t tail_vertices = 65536;
+    int32_t tail_vertices = 4096;
     pgc_profile* profile = nullptr;
 };
 pgc_status read_opts(const pgc_opts* in, Opts* out);
