@@ -211,6 +211,22 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job ends when every replica has)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Units all replicas processed per second (each rank colors its own copy)."""
+    return world * units_per_rank / (ms_per_step / 1000.0)
+
+
 def bench_batch(pgc, inputs, torch, dev, num_graphs):
     """The batched form vs one plain pgc_color_d1 call per graph, inputs
     resident on the device, identical colorings checked."""
@@ -500,13 +516,9 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_per_step = ms / args.steps
-    value = world * m / (ms_per_step / 1000.0)
+    value = whole_job_rate(m, world, ms_per_step)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
@@ -558,11 +570,17 @@ def main():
         avg_s = prof.kernel_ms[top] / 1000.0 / launches
         per_launch = nbytes[top] / launches
         achieved = per_launch / avg_s / 1e9
+        # DRAM bytes per launch from an ncu capture (profiles/traffic.json),
+        # used only while the kernel source is the one that was measured
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
+            import hashlib
             tr = json.load(open(tpath)).get(top)
-            if tr and tr.get("workload") == f"rmat{args.scale}":
+            src = os.path.join(ROOT, "paper_2107_00075_gb300", "csrc", "d1_engine.cuh")
+            cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            if (tr and tr.get("workload") == f"rmat{args.scale}"
+                    and tr.get("kernel_source_sha256") == cur):
                 traffic = tr.get("bytes_per_launch")
         roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

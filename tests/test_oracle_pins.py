@@ -373,3 +373,27 @@ def test_self_loops_and_duplicates_tolerated():
     assert oracle.count_improper(oracle.D1, rp, ci, r.colors) == 0
     # vertex 0 has degree 3 (self-loop and duplicate counted) > deg(1) = 2
     assert r.colors[0] == 1
+
+
+# ---------------------------------------------------------------- checkers ---
+def test_checkers_on_hand_colorings():
+    """The properness and Grundy checkers against colorings checked by hand."""
+    g = gen.path(3)                       # 0 - 1 - 2
+    D1 = oracle.D1
+    assert oracle.count_improper(D1, g.row_ptr, g.col_idx, [1, 2, 1]) == 0
+    assert oracle.count_improper(D1, g.row_ptr, g.col_idx, [1, 1, 2]) == 2   # (0,1) and (1,0)
+    assert oracle.count_improper(D1, g.row_ptr, g.col_idx, [1, 0, 1]) == 1   # uncolored vertex
+    assert oracle.count_non_grundy(D1, g.row_ptr, g.col_idx, [2, 1, 2]) == 0
+    assert oracle.count_non_grundy(D1, g.row_ptr, g.col_idx, [1, 2, 3]) == 1  # 2 sees only 2
+    assert oracle.count_non_grundy(D1, g.row_ptr, g.col_idx, [3, 1, 2]) == 1  # 0 sees only 1
+    # distance 2: on the path every pair is within two hops
+    assert oracle.count_improper(oracle.D2, g.row_ptr, g.col_idx, [2, 1, 2]) == 2
+    assert oracle.count_improper(oracle.D2, g.row_ptr, g.col_idx, [3, 1, 2]) == 0
+    assert oracle.count_non_grundy(oracle.D2, g.row_ptr, g.col_idx, [3, 1, 2]) == 0
+    # partial distance 2: rows {0,1} and {1,2}; columns 0 and 2 share no row
+    b = _graphs.bipartite_from_rows([[0, 1], [1, 2]], 3)
+    kw = dict(n_rows=2, n_cols=3, col_ptr=b.col_ptr, row_idx=b.row_idx)
+    assert oracle.count_improper(oracle.PD2, b.row_ptr, b.col_idx, [2, 1, 2], **kw) == 0
+    assert oracle.count_improper(oracle.PD2, b.row_ptr, b.col_idx, [1, 1, 2], **kw) == 2
+    assert oracle.count_non_grundy(oracle.PD2, b.row_ptr, b.col_idx, [2, 1, 2], **kw) == 0
+    assert oracle.count_non_grundy(oracle.PD2, b.row_ptr, b.col_idx, [3, 1, 2], **kw) == 1  # column 0
