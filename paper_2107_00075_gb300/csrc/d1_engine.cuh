@@ -77,6 +77,12 @@ struct SingleView {
         d = __ldg(rp + v + 1) - r0;
     }
     __device__ __forceinline__ int nbr(long long e, int) const { return __ldg(ci + e); }
+    // start of v's row relative to its graph, and the absolute start from it
+    __device__ __forceinline__ void local_row(int v, int, int& r0, int& d) const {
+        r0 = __ldg(rp + v);
+        d = __ldg(rp + v + 1) - r0;
+    }
+    __device__ __forceinline__ long long begin(int, int r0) const { return r0; }
 };
 
 // A batch: graph-local row_ptr blocks (n_g + 1 entries each) and graph-local
@@ -96,6 +102,13 @@ struct BatchView {
     }
     __device__ __forceinline__ int nbr(long long e, int base_g) const {
         return base_g + __ldg(ci + e);
+    }
+    __device__ __forceinline__ void local_row(int v, int g, int& r0, int& d) const {
+        r0 = __ldg(rp + v + g);
+        d = __ldg(rp + v + g + 1) - r0;
+    }
+    __device__ __forceinline__ long long begin(int g, int r0) const {
+        return __ldg(nnz_off + g) + r0;
     }
 };
 
@@ -138,9 +151,11 @@ struct Problem {
     int* hadj;                 // H(v) stored at hadj[row start of v ...]
     unsigned long long* bm0;   // forbidden colors 1..64, one word per vertex
     unsigned* bmx;             // forbidden colors 65..deg+1 (deg >= 64)
-    int* ws[2];                // S-tier worklists per parity
-    int* wm[2];                // M-tier worklists
-    int* wl[2];                // L-tier worklists
+    // worklists per parity; an entry is {v, |H(v)|, deg(v), row start of v
+    // within its graph}, so a scan needs no further lookup to begin
+    int4* ws[2];               // S tier
+    int4* wm[2];               // M tier
+    int4* wl[2];               // L tier
     int2* items;               // setup: (vertex, item) list for long rows
     int2* push_q;              // (vertex, item) push work
     int* g_rounds;             // batch: rounds per graph (nullable)
@@ -212,19 +227,20 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
     const Problem<V>& P = *Pp;
     State* st = P.st;
     const int warp = threadIdx.x >> 5;
-    WarpAppend as = {smem + warp * 128, 0}, am = {smem + warp * 128 + 64, 0};
+    int4* sm4 = reinterpret_cast<int4*>(smem);
+    WarpAppend4 as = {sm4 + warp * 128, 0}, am = {sm4 + warp * 128 + 64, 0};
     const int n = P.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
          wbase += stride) {
         const long long i = wbase + lane_id();
         const bool valid = i < n;
-        int d = -1;
+        int d = -1, r0 = 0;
         if (valid) {
             const int v = (int)i;
             const int g = P.g.graph(v);
-            long long b;
-            P.g.row(v, g, b, d);
+            P.g.local_row(v, g, r0, d);
+            const long long b = P.g.begin(g, r0);
             P.deg[v] = d;
             P.col[v] = -1;
             P.hlen[v] = 0;
@@ -239,11 +255,12 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
                 for (int k = 0; k < nit; ++k) P.items[base + k] = make_int2(v, k);
             }
         }
-        wa_push(as, valid && d <= kBuildS, (int)i, P.ws[0], &st->bs);
-        wa_push(am, valid && d > kBuildS && d <= kBuildM, (int)i, P.wm[0], &st->bm);
+        const int4 ent = make_int4((int)i, 0, d, r0);
+        wa4_push(as, valid && d <= kBuildS, ent, P.ws[0], &st->bs);
+        wa4_push(am, valid && d > kBuildS && d <= kBuildM, ent, P.wm[0], &st->bm);
     }
-    wa_flush(as, P.ws[0], &st->bs);
-    wa_flush(am, P.wm[0], &st->bm);
+    wa4_flush(as, P.ws[0], &st->bs);
+    wa4_flush(am, P.wm[0], &st->bm);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->round = 1;
         st->t0 = global_ns();
@@ -299,11 +316,10 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
 
     // medium rows: one warp per vertex, ordered compaction by ballot
     for (int i = gw; i < nM; i += nw) {
-        const int v = P.wm[0][i];
+        const int4 ent = P.wm[0][i];
+        const int v = ent.x, d = ent.z;
         const int g = P.g.graph(v), base = P.g.base(g);
-        long long beg;
-        int d;
-        P.g.row(v, g, beg, d);
+        const long long beg = P.g.begin(g, ent.w);
         const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
         int pos = 0;
         for (int b0 = 0; b0 < d; b0 += 32) {
@@ -327,11 +343,10 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
     // short rows: one thread per vertex
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += stride) {
-        const int v = P.ws[0][i];
+        const int4 ent = P.ws[0][i];
+        const int v = ent.x, d = ent.z;
         const int g = P.g.graph(v), base = P.g.base(g);
-        long long beg;
-        int d;
-        P.g.row(v, g, beg, d);
+        const long long beg = P.g.begin(g, ent.w);
         const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
         int pos = 0;
         for (int e = 0; e < d; ++e) {
@@ -348,16 +363,24 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
 
 // Append v to the worklist of its H-list tier (all 32 lanes call).
 struct TierAppend {
-    WarpAppend s, m;
+    WarpAppend4 s, m;
 };
 
+__device__ __forceinline__ TierAppend tier_appender(int* smem) {
+    int4* sm4 = reinterpret_cast<int4*>(smem);
+    const int warp = threadIdx.x >> 5;
+    return TierAppend{{sm4 + warp * 128, 0}, {sm4 + warp * 128 + 64, 0}};
+}
+
+// e = {v, |H(v)|, deg(v), local row start}
 template <class V>
-__device__ __forceinline__ void tier_push(const Problem<V>& P, TierAppend& a, bool pred, int v,
-                                          int hl, int p) {
+__device__ __forceinline__ void tier_push(const Problem<V>& P, TierAppend& a, bool pred, int4 e,
+                                          int p) {
     State* st = P.st;
-    wa_push(a.s, pred && hl <= P.det_s, v, P.ws[p], &st->ns[p]);
-    wa_push(a.m, pred && hl > P.det_s && hl <= P.det_m, v, P.wm[p], &st->nm[p]);
-    if (pred && hl > P.det_m) P.wl[p][atomicAdd(&st->nl[p], 1)] = v;
+    const int hl = e.y;
+    wa4_push(a.s, pred && hl <= P.det_s, e, P.ws[p], &st->ns[p]);
+    wa4_push(a.m, pred && hl > P.det_s && hl <= P.det_m, e, P.wm[p], &st->nm[p]);
+    if (pred && hl > P.det_m) P.wl[p][atomicAdd(&st->nl[p], 1)] = e;
 }
 
 // ---------------------------------------------------------------------------
@@ -367,19 +390,23 @@ template <class V>
 __global__ void d1_tier(const Problem<V>* __restrict__ Pp) {
     extern __shared__ int smem[];
     const Problem<V>& P = *Pp;
-    const int warp = threadIdx.x >> 5;
-    TierAppend a = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
+    TierAppend a = tier_appender(smem);
     const int n = P.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
          wbase += stride) {
         const long long i = wbase + lane_id();
         const bool valid = i < n;
-        const int hl = valid ? P.hlen[i] : 0;
-        tier_push(P, a, valid, (int)i, hl, 1);
+        int4 e = make_int4((int)i, 0, 0, 0);
+        if (valid) {
+            int r0, d;
+            P.g.local_row((int)i, P.g.graph((int)i), r0, d);
+            e = make_int4((int)i, P.hlen[i], d, r0);
+        }
+        tier_push(P, a, valid, e, 1);
     }
-    wa_flush(a.s, P.ws[1], &P.st->ns[1]);
-    wa_flush(a.m, P.wm[1], &P.st->nm[1]);
+    wa4_flush(a.s, P.ws[1], &P.st->ns[1]);
+    wa4_flush(a.m, P.wm[1], &P.st->nm[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,8 +440,8 @@ __device__ __forceinline__ void assign_phase(const Problem<V>& P) {
     const long long total = (long long)n0 + n1 + n2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int v = i < n0 ? P.ws[cp][i]
-                    : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
+        const int v = i < n0 ? P.ws[cp][i].x
+                    : (i < n0 + n1 ? P.wm[cp][i - n0].x : P.wl[cp][i - n0 - n1].x);
         assign_one(P, v);
     }
 }
@@ -529,59 +556,48 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
     int my_max = 0;
     unsigned long long my_s = 0ull, my_h = 0ull;
-    TierAppend app = {{smem + warp * 128, 0}, {smem + warp * 128 + 64, 0}};
+    TierAppend app = tier_appender(smem);
 
-    // --- L tier: one block per vertex ---
-    __shared__ int s_idx;
-    if (nL > 0) {
-        for (;;) {
-            if (threadIdx.x == 0) s_idx = (int)atomicAdd(&st->l_next, 1u);
-            __syncthreads();
-            const int i = s_idx;
-            if (i >= nL) break;
-            const int v = P.wl[cp][i];
-            const int g = P.g.graph(v);
-            long long beg;
-            int d;
-            P.g.row(v, g, beg, d);
-            const int hl = P.hlen[v];
-            const int t = -col[v];
-            bool lose = false;
-            int nxt = (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
-            for (int b0 = 0; b0 < hl; b0 += blockDim.x) {
-                const int u = nxt;
-                const int e = b0 + blockDim.x + threadIdx.x;
-                nxt = e < hl ? __ldg(ha + beg + e) : -1;
-                if (__syncthreads_or(u >= 0 && abs(col[u]) == t)) {
-                    lose = true;
-                    break;
-                }
+    // --- L tier: one block per vertex (static assignment) ---
+    for (int i = blockIdx.x; i < nL; i += gridDim.x) {
+        const int4 ent = P.wl[cp][i];
+        const int v = ent.x, hl = ent.y, d = ent.z;
+        const int g = P.g.graph(v);
+        const long long beg = P.g.begin(g, ent.w);
+        const int t = -col[v];
+        bool lose = false;
+        int nxt = (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
+        for (int b0 = 0; b0 < hl; b0 += blockDim.x) {
+            const int u = nxt;
+            const int e = b0 + blockDim.x + threadIdx.x;
+            nxt = e < hl ? __ldg(ha + beg + e) : -1;
+            if (__syncthreads_or(u >= 0 && abs(col[u]) == t)) {
+                lose = true;
+                break;
             }
-            if (threadIdx.x == 0) {
-                if (lose) {
-                    P.wl[np][atomicAdd(&st->nl[np], 1)] = v;
-                    my_s += (unsigned long long)d;
-                    my_h += (unsigned long long)hl;
-                    if (batch) atomicMax(P.g_rounds + g, r + 1);
-                } else {
-                    col[v] = t;
-                    my_max = max(my_max, t);
-                    if (batch) atomicMax(P.g_colors + g, t);
-                    queue_push(P, v, d);
-                }
-            }
-            __syncthreads();
         }
+        if (threadIdx.x == 0) {
+            if (lose) {
+                P.wl[np][atomicAdd(&st->nl[np], 1)] = ent;
+                my_s += (unsigned long long)d;
+                my_h += (unsigned long long)hl;
+                if (batch) atomicMax(P.g_rounds + g, r + 1);
+            } else {
+                col[v] = t;
+                my_max = max(my_max, t);
+                if (batch) atomicMax(P.g_colors + g, t);
+                queue_push(P, v, d);
+            }
+        }
+        __syncthreads();
     }
 
     // --- M tier: one warp per vertex ---
     for (int i = gw; i < nM; i += nw) {
-        const int v = P.wm[cp][i];
+        const int4 ent = P.wm[cp][i];
+        const int v = ent.x, hl = ent.y, d = ent.z;
         const int g = P.g.graph(v);
-        long long beg;
-        int d;
-        P.g.row(v, g, beg, d);
-        const int hl = P.hlen[v];
+        const long long beg = P.g.begin(g, ent.w);
         const int t = -col[v];
         const bool lose = warp_conflict(P, beg, hl, t);
         if (lane == 0) {
@@ -596,7 +612,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 queue_push(P, v, d);
             }
         }
-        tier_push(P, app, lose && lane == 0, v, hl, np);
+        tier_push(P, app, lose && lane == 0, ent, np);
     }
 
     // --- S tier: one thread per vertex ---
@@ -605,16 +621,15 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
          wbase += stride) {
         const long long i = wbase + lane;
         bool lose = false, win = false;
-        int v = -1, hl = 0, g = 0, t = 0;
+        int g = 0, t = 0;
+        int4 ent = make_int4(-1, 0, 0, 0);
         if (i < nS) {
-            v = P.ws[cp][i];
+            ent = P.ws[cp][i];
+            const int v = ent.x, hl = ent.y, d = ent.z;
             g = P.g.graph(v);
-            long long beg;
-            int d;
-            P.g.row(v, g, beg, d);
-            hl = P.hlen[v];
-            t = -col[v];
+            const long long beg = P.g.begin(g, ent.w);
             int nxt = hl > 0 ? __ldg(ha + beg) : -1;
+            t = -col[v];
             for (int e = 0; e < hl; ++e) {
                 const int u = nxt;
                 nxt = e + 1 < hl ? __ldg(ha + beg + e + 1) : -1;
@@ -645,10 +660,10 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             graph_max(P.g_rounds, lose, g, r + 1);
             graph_max(P.g_colors, win, g, t);
         }
-        tier_push(P, app, lose, v, hl, np);
+        tier_push(P, app, lose, ent, np);
     }
-    wa_flush(app.s, P.ws[np], &st->ns[np]);
-    wa_flush(app.m, P.wm[np], &st->nm[np]);
+    wa4_flush(app.s, P.ws[np], &st->ns[np]);
+    wa4_flush(app.m, P.wm[np], &st->nm[np]);
 
     // --- per-warp totals ---
     my_max = warp_max(my_max);
@@ -796,9 +811,9 @@ struct Scratch {
     int* hadj;
     unsigned long long* bm0;
     unsigned* bmx;
-    int* ws;     // 2n: both parities
-    int* wm;
-    int* wl;
+    int4* ws;    // 2n entries: both parities
+    int4* wm;
+    int4* wl;
     int2* items;
     int2* pushq;
 };
@@ -817,7 +832,7 @@ inline ScratchSizes scratch_sizes(long long n, long long nnz) {
     z.hadj = (size_t)std::max<long long>(nnz, 1) * 4;
     z.bm0 = (size_t)n * 8;
     z.bmx = ((size_t)(nnz >> 5) + (size_t)n + 1) * 4;
-    z.list = (size_t)n * 4 * 2;
+    z.list = (size_t)n * sizeof(int4) * 2;
     z.items = ((size_t)n + (size_t)(nnz / kBuildItem) + 1) * sizeof(int2);
     z.pushq = ((size_t)n + (size_t)(nnz / kPushItem) + 1) * sizeof(int2);
     return z;
@@ -838,9 +853,9 @@ inline Scratch carve_scratch(void* base, long long n, long long nnz) {
     sc.hadj = reinterpret_cast<int*>(take(z.hadj));
     sc.bm0 = reinterpret_cast<unsigned long long*>(take(z.bm0));
     sc.bmx = reinterpret_cast<unsigned*>(take(z.bmx));
-    sc.ws = reinterpret_cast<int*>(take(z.list));
-    sc.wm = reinterpret_cast<int*>(take(z.list));
-    sc.wl = reinterpret_cast<int*>(take(z.list));
+    sc.ws = reinterpret_cast<int4*>(take(z.list));
+    sc.wm = reinterpret_cast<int4*>(take(z.list));
+    sc.wl = reinterpret_cast<int4*>(take(z.list));
     sc.items = reinterpret_cast<int2*>(take(z.items));
     sc.pushq = reinterpret_cast<int2*>(take(z.pushq));
     return sc;
@@ -882,7 +897,7 @@ struct Engine {
 
     pgc_status geometry(const Opts& o, Geometry* g) {
         g->block = o.block;
-        g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
+        g->smem = (size_t)(o.block / 32) * 128 * sizeof(int4);
         int per_sm = o.grid_per_sm;
         if (per_sm == 0) {
             int a = 0, b = 0;
@@ -984,9 +999,9 @@ struct Engine {
         sc.hadj = hadj.as<int>();
         sc.bm0 = bm0.as<unsigned long long>();
         sc.bmx = bmx.as<unsigned>();
-        sc.ws = ws.as<int>();
-        sc.wm = wm.as<int>();
-        sc.wl = wl.as<int>();
+        sc.ws = ws.as<int4>();
+        sc.wm = wm.as<int4>();
+        sc.wl = wl.as<int4>();
         sc.items = items.as<int2>();
         sc.pushq = pushq.as<int2>();
         if (pgc_status s = launch(sc, view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream))

@@ -103,3 +103,46 @@ __device__ __forceinline__ long long bitmap_offset(int rp_v, int v) {
 }
 
 }  // namespace pgc
+
+namespace pgc {
+
+// WarpAppend for 16-byte entries (a 64-entry int4 buffer per warp).
+struct WarpAppend4 {
+    int4* buf;
+    int count;
+};
+
+__device__ __forceinline__ void wa4_push(WarpAppend4& a, bool pred, int4 e, int4* out,
+                                         int* out_cnt) {
+    const unsigned lane = lane_id();
+    const unsigned m = __ballot_sync(kFullMask, pred);
+    if (pred) a.buf[a.count + __popc(m & ((1u << lane) - 1u))] = e;
+    a.count += __popc(m);
+    __syncwarp();
+    if (a.count >= 32) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(out_cnt, 32);
+        base = __shfl_sync(kFullMask, base, 0);
+        out[base + lane] = a.buf[lane];
+        const int rem = a.count - 32;
+        int4 tmp = make_int4(0, 0, 0, 0);
+        if ((int)lane < rem) tmp = a.buf[32 + lane];
+        __syncwarp();
+        if ((int)lane < rem) a.buf[lane] = tmp;
+        a.count = rem;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void wa4_flush(WarpAppend4& a, int4* out, int* out_cnt) {
+    if (a.count == 0) return;
+    const unsigned lane = lane_id();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(out_cnt, a.count);
+    base = __shfl_sync(kFullMask, base, 0);
+    if ((int)lane < a.count) out[base + lane] = a.buf[lane];
+    a.count = 0;
+    __syncwarp();
+}
+
+}  // namespace pgc

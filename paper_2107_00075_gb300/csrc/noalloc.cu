@@ -35,13 +35,13 @@ struct NoAllocLayout {
     static constexpr size_t bm0 = align256(hadj + 4 * nnz);
     static constexpr size_t bmx = align256(bm0 + 8 * n);
     static constexpr size_t lists = align256(bmx + 4 * ((nnz >> 5) + n + 1));
-    static constexpr size_t items = align256(lists + 4 * n * 6);
+    static constexpr size_t items = align256(lists + 16 * n * 6);
     static constexpr size_t pushq = align256(items + 8 * (n + nnz / kBuildItem + 1));
     static constexpr size_t trace = align256(pushq + 8 * (n + nnz / kPushItem + 1));
     static constexpr size_t total = align256(trace + 3 * sizeof(long long));
 };
 
-// The scratch itself (about 4 MB).  In host code this name is only a
+// The scratch itself (about 7 MB).  In host code this name is only a
 // stand-in for the device object; its device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
@@ -109,7 +109,7 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
     hp.hadj = reinterpret_cast<int*>(base + L::hadj);
     hp.bm0 = reinterpret_cast<unsigned long long*>(base + L::bm0);
     hp.bmx = reinterpret_cast<unsigned*>(base + L::bmx);
-    int* lists = reinterpret_cast<int*>(base + L::lists);
+    int4* lists = reinterpret_cast<int4*>(base + L::lists);
     for (int p = 0; p < 2; ++p) {
         hp.ws[p] = lists + (size_t)(0 + p) * nn;
         hp.wm[p] = lists + (size_t)(2 + p) * nn;
@@ -136,7 +136,7 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
 
     const int block = 256;
     const int grid = sms * 4;
-    const size_t smem = (size_t)(block / 32) * 128 * sizeof(int);
+    const size_t smem = (size_t)(block / 32) * 128 * sizeof(int4);
     const cudaGraphConditionalHandle none = 0;
     d1_classify<SingleView><<<grid, block, smem, stream>>>(dP);
     d1_build<SingleView><<<grid, block, 0, stream>>>(dP);
