@@ -898,6 +898,12 @@ struct Engine {
     pgc_status geometry(const Opts& o, Geometry* g) {
         g->block = o.block;
         g->smem = (size_t)(o.block / 32) * 128 * sizeof(int4);
+        if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
+            for (const void* f : {(const void*)d1_classify<V>, (const void*)d1_tier<V>,
+                                  (const void*)d1_detect<V>, (const void*)d1_tail<V>})
+                PGC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)g->smem));
+        }
         int per_sm = o.grid_per_sm;
         if (per_sm == 0) {
             int a = 0, b = 0;
