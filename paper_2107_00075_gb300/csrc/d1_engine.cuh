@@ -151,6 +151,7 @@ struct Problem {
     int* hadj;                 // H(v) stored at hadj[row start of v ...]
     unsigned long long* bm0;   // forbidden colors 1..64, one word per vertex
     unsigned* bmx;             // forbidden colors 65..deg+1 (deg >= 64)
+    unsigned* live;            // bit v set while v is uncolored
     // worklists per parity; an entry is {v, |H(v)|, deg(v), row start of v
     // within its graph}, so a scan needs no further lookup to begin
     int4* ws[2];               // S tier
@@ -197,6 +198,8 @@ __device__ __forceinline__ long long bm_offset(long long row_begin, int v) {
 // need no check and the update is a fire-and-forget reduction.
 template <class V>
 __device__ __forceinline__ void push_color(const Problem<V>& P, int u, int g, int c) {
+    // most neighbors of a late winner are colored already: skip them
+    if (!((P.live[u >> 5] >> (u & 31)) & 1u)) return;
     if (c <= 64) {
         atomicOr(P.bm0 + u, 1ull << (c - 1));
         return;
@@ -255,6 +258,8 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
                 for (int k = 0; k < nit; ++k) P.items[base + k] = make_int2(v, k);
             }
         }
+        const unsigned vm = __ballot_sync(kFullMask, valid);
+        if (lane_id() == 0) P.live[wbase >> 5] = vm;   // wbase is a multiple of 32
         const int4 ent = make_int4((int)i, 0, d, r0);
         wa4_push(as, valid && d <= kBuildS, ent, P.ws[0], &st->bs);
         wa4_push(am, valid && d > kBuildS && d <= kBuildM, ent, P.wm[0], &st->bm);
@@ -584,6 +589,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 if (batch) atomicMax(P.g_rounds + g, r + 1);
             } else {
                 col[v] = t;
+                atomicAnd(P.live + (v >> 5), ~(1u << (v & 31)));
                 my_max = max(my_max, t);
                 if (batch) atomicMax(P.g_colors + g, t);
                 queue_push(P, v, d);
@@ -607,6 +613,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 if (batch) atomicMax(P.g_rounds + g, r + 1);
             } else {
                 col[v] = t;
+                atomicAnd(P.live + (v >> 5), ~(1u << (v & 31)));
                 my_max = max(my_max, t);
                 if (batch) atomicMax(P.g_colors + g, t);
                 queue_push(P, v, d);
@@ -644,6 +651,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             } else {
                 win = true;
                 col[v] = t;
+                atomicAnd(P.live + (v >> 5), ~(1u << (v & 31)));
                 my_max = max(my_max, t);
                 if (d <= kInlinePush) {
                     const int base = P.g.base(g);
@@ -811,6 +819,7 @@ struct Scratch {
     int* hadj;
     unsigned long long* bm0;
     unsigned* bmx;
+    unsigned* live;
     int4* ws;    // 2n entries: both parities
     int4* wm;
     int4* wl;
@@ -819,10 +828,11 @@ struct Scratch {
 };
 
 struct ScratchSizes {
-    size_t deg, hlen, hadj, bm0, bmx, list, items, pushq;
+    size_t deg, hlen, hadj, bm0, bmx, live, list, items, pushq;
     size_t total() const {   // with 256-byte alignment of every buffer
         auto a = [](size_t x) { return (x + 255) / 256 * 256; };
-        return a(deg) + a(hlen) + a(hadj) + a(bm0) + a(bmx) + 3 * a(list) + a(items) + a(pushq);
+        return a(deg) + a(hlen) + a(hadj) + a(bm0) + a(bmx) + a(live) + 3 * a(list) + a(items) +
+               a(pushq);
     }
 };
 
@@ -832,6 +842,7 @@ inline ScratchSizes scratch_sizes(long long n, long long nnz) {
     z.hadj = (size_t)std::max<long long>(nnz, 1) * 4;
     z.bm0 = (size_t)n * 8;
     z.bmx = ((size_t)(nnz >> 5) + (size_t)n + 1) * 4;
+    z.live = ((size_t)n / 32 + 2) * 4;
     z.list = (size_t)n * sizeof(int4) * 2;
     z.items = ((size_t)n + (size_t)(nnz / kBuildItem) + 1) * sizeof(int2);
     z.pushq = ((size_t)n + (size_t)(nnz / kPushItem) + 1) * sizeof(int2);
@@ -853,6 +864,7 @@ inline Scratch carve_scratch(void* base, long long n, long long nnz) {
     sc.hadj = reinterpret_cast<int*>(take(z.hadj));
     sc.bm0 = reinterpret_cast<unsigned long long*>(take(z.bm0));
     sc.bmx = reinterpret_cast<unsigned*>(take(z.bmx));
+    sc.live = reinterpret_cast<unsigned*>(take(z.live));
     sc.ws = reinterpret_cast<int4*>(take(z.list));
     sc.wm = reinterpret_cast<int4*>(take(z.list));
     sc.wl = reinterpret_cast<int4*>(take(z.list));
@@ -864,7 +876,7 @@ template <class V>
 struct Engine {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf deg, hlen, hadj, bm0, bmx, ws, wm, wl, items, pushq, state, problem, trace;
+    DevBuf deg, hlen, hadj, bm0, bmx, live, ws, wm, wl, items, pushq, state, problem, trace;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     int last_want_trace = 0, last_tcap = 1;
@@ -882,8 +894,8 @@ struct Engine {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &ws, &wm, &wl, &items, &pushq, &state,
-                          &problem, &trace})
+        for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &live, &ws, &wm, &wl, &items, &pushq,
+                          &state, &problem, &trace})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
         trace_cap = 0;
@@ -994,6 +1006,7 @@ struct Engine {
         if (pgc_status s = hadj.ensure(z.hadj)) return s;
         if (pgc_status s = bm0.ensure(z.bm0)) return s;
         if (pgc_status s = bmx.ensure(z.bmx)) return s;
+        if (pgc_status s = live.ensure(z.live)) return s;
         if (pgc_status s = ws.ensure(z.list)) return s;
         if (pgc_status s = wm.ensure(z.list)) return s;
         if (pgc_status s = wl.ensure(z.list)) return s;
@@ -1005,6 +1018,7 @@ struct Engine {
         sc.hadj = hadj.as<int>();
         sc.bm0 = bm0.as<unsigned long long>();
         sc.bmx = bmx.as<unsigned>();
+        sc.live = live.as<unsigned>();
         sc.ws = ws.as<int4>();
         sc.wm = wm.as<int4>();
         sc.wl = wl.as<int4>();
@@ -1049,6 +1063,7 @@ struct Engine {
         hp->hadj = sc.hadj;
         hp->bm0 = sc.bm0;
         hp->bmx = sc.bmx;
+        hp->live = sc.live;
         for (int p = 0; p < 2; ++p) {
             hp->ws[p] = sc.ws + (size_t)p * n;
             hp->wm[p] = sc.wm + (size_t)p * n;

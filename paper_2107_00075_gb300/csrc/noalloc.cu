@@ -34,7 +34,8 @@ struct NoAllocLayout {
     static constexpr size_t hadj = align256(hlen + 4 * n);
     static constexpr size_t bm0 = align256(hadj + 4 * nnz);
     static constexpr size_t bmx = align256(bm0 + 8 * n);
-    static constexpr size_t lists = align256(bmx + 4 * ((nnz >> 5) + n + 1));
+    static constexpr size_t live = align256(bmx + 4 * ((nnz >> 5) + n + 1));
+    static constexpr size_t lists = align256(live + 4 * (n / 32 + 2));
     static constexpr size_t items = align256(lists + 16 * n * 6);
     static constexpr size_t pushq = align256(items + 8 * (n + nnz / kBuildItem + 1));
     static constexpr size_t trace = align256(pushq + 8 * (n + nnz / kPushItem + 1));
@@ -109,6 +110,7 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
     hp.hadj = reinterpret_cast<int*>(base + L::hadj);
     hp.bm0 = reinterpret_cast<unsigned long long*>(base + L::bm0);
     hp.bmx = reinterpret_cast<unsigned*>(base + L::bmx);
+    hp.live = reinterpret_cast<unsigned*>(base + L::live);
     int4* lists = reinterpret_cast<int4*>(base + L::lists);
     for (int p = 0; p < 2; ++p) {
         hp.ws[p] = lists + (size_t)(0 + p) * nn;
