@@ -48,7 +48,7 @@ struct State {
     int max_color;
     int nt[2];        // thread-tier worklist sizes per parity
     int nw[2];        // warp-tier worklist sizes
-    int pad0;
+    int all_active;   // this round every net is treated as active (no marking)
     unsigned blocks_done;
     int bound;        // max over v of sum over its nets of (|net| - 1)
     int pad;
@@ -99,14 +99,6 @@ __device__ __forceinline__ int vertex_net(const Problem& P, int v, int beg, int 
     return __ldg(P.r_idx + beg + k);
 }
 
-__device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v,
-                                       unsigned long long seed, bool use_deg) {
-    if (use_deg && du != dv) return du > dv;
-    const uint64_t hu = prio_hash(seed, (uint32_t)u);
-    if (hu != hv) return hu < hv;
-    return u < v;
-}
-
 // ---------------------------------------------------------------------------
 // init: degrees, empty colors, worklists by number of nets, the color bound
 // ---------------------------------------------------------------------------
@@ -152,6 +144,7 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->round = 1;
+        st->all_active = 1;
         st->t0 = global_ns();
         if (P.trace_cap > 0) {
             P.trace_w[0] = P.n;
@@ -176,6 +169,7 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
     const int r = *(volatile int*)&st->round;
     const int cp = r & 1;
     const int nT = st->nt[cp], nW = st->nw[cp];
+    const bool mark = *(volatile int*)&st->all_active == 0;
     const unsigned long long* mk = P.mask;
     const long long nn = P.n_nets;
     // thread tier
@@ -195,7 +189,8 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
             t = 64 * P.windows;
         }
         P.col[v] = -t;
-        for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
+        if (mark)
+            for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
     }
     // warp tier
     const int lane = lane_id(), wpb = blockDim.x >> 5;
@@ -217,7 +212,8 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
             t = 64 * P.windows;
         }
         if (lane == 0) P.col[v] = -t;
-        for (int j = lane; j < k; j += 32) mark_net(P, vertex_net(P, v, beg, j), r);
+        if (mark)
+            for (int j = lane; j < k; j += 32) mark_net(P, vertex_net(P, v, beg, j), r);
     }
 }
 
@@ -225,82 +221,197 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
 // detect: per active net, flag members that share a color with a member of
 // higher priority.  Members holding a committed (positive) color never
 // match: first fit excluded every committed color of v's nets.
+//
+// Within one net, the members holding tentative color c form a group; every
+// member of the group except its highest-priority one is recolored (Alg. 4
+// applied to each pair of the group).  So a group needs no pairwise loop:
+// three warp reductions (largest degree, smallest hash, smallest id) find
+// its winner.  Small nets (2..32 members) are packed whole into "rows" of
+// 32 lanes -- several nets per row -- and four rows are loaded at once so a
+// warp keeps many independent gathers in flight.  Larger nets compare every
+// member against every other member, 32 x 32 at a time.
 // ---------------------------------------------------------------------------
-__global__ void net_detect(const Problem* __restrict__ Pp) {
-    const Problem& P = *Pp;
-    const int r = *(volatile int*)&P.st->round;
-    const int lane = lane_id(), wpb = blockDim.x >> 5;
+constexpr int kDetRows = 4;        // rows loaded together
+constexpr int kDetSmemInts = 97;   // per warp: 32 net ids, 32 m_ptr, 33 packed starts
+
+__device__ __forceinline__ unsigned lanemask_le() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+// g: the lanes (this one included) holding this lane's tentative color in
+// the same net.  True if one of them has priority over this lane's x.
+__device__ __forceinline__ bool group_loses(unsigned g, int x, int d, unsigned long long seed,
+                                            bool use_deg) {
+    if (use_deg) {
+        const unsigned md = __reduce_max_sync(g, (unsigned)d);
+        const unsigned g2 = __ballot_sync(g, (unsigned)d == md) & g;
+        if ((unsigned)d != md) return true;
+        g = g2;
+        if (__popc(g) == 1) return false;
+    }
+    const uint64_t h = prio_hash(seed, (uint32_t)x);
+    const unsigned hi = (unsigned)(h >> 32), lo = (unsigned)h;
+    const unsigned mh = __reduce_min_sync(g, hi);
+    const unsigned g3 = __ballot_sync(g, hi == mh) & g;
+    if (hi != mh) return true;
+    if (__popc(g3) == 1) return false;
+    const unsigned ml = __reduce_min_sync(g3, lo);
+    const unsigned g4 = __ballot_sync(g3, lo == ml) & g3;
+    if (lo != ml) return true;
+    if (__popc(g4) == 1) return false;
+    // equal keys: the same vertex listed twice, or the smaller id wins
+    return (unsigned)x != __reduce_min_sync(g4, (unsigned)x);
+}
+
+__device__ void big_net_detect(const Problem& P, int q, int m, int lane) {
     const unsigned long long seed = P.seed;
     const bool use_deg = P.use_deg != 0;
-    const int nn = P.n_nets;
-    // each warp reads 32 net flags at a time and handles the active ones
-    for (long long b0 = ((long long)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; b0 < nn;
-         b0 += (long long)gridDim.x * wpb * 32) {
-      unsigned act = __ballot_sync(kFullMask, b0 + lane < nn && P.net_flag[b0 + lane] == r);
-      while (act) {
-        const int q = (int)b0 + __ffs(act) - 1;
-        act &= act - 1;
-        const int m = net_size(P, q);
-        if (m <= 32) {
-            int x = -1, c = 0, d = 0;
-            if (lane < m) {
-                x = net_member(P, q, lane);
-                const int cx = P.col[x];
-                c = cx < 0 ? -cx : 0;   // only uncolored members can conflict
-                if (c) d = __ldg(P.deg + x);
-            }
-            // lanes holding the same uncolored color as some other lane
-            const unsigned grp = __match_any_sync(kFullMask, c) & ~(1u << lane);
-            // each such lane broadcasts (id, color, degree); every uncolored
-            // lane of the same color checks whether the source has priority
-            bool lose = false;
-            const uint64_t hx = c ? prio_hash(seed, (uint32_t)x) : 0ull;
-            unsigned any = __ballot_sync(kFullMask, c != 0 && grp != 0);
-            while (any) {
-                const int src = __ffs(any) - 1;
-                any &= any - 1;
-                const int xs = __shfl_sync(kFullMask, x, src);
-                const int cs = __shfl_sync(kFullMask, c, src);
-                const int ds = __shfl_sync(kFullMask, d, src);
-                if (c && src != lane && cs == c && xs != x && higher(ds, xs, d, hx, x, seed, use_deg))
-                    lose = true;
-            }
-            if (lose) P.lose[x] = 1;
-        } else {
-            // large net: every uncolored member against every other member
-            for (int i0 = 0; i0 < m; i0 += 32) {
-                int x = -1, c = 0, d = 0;
-                if (i0 + lane < m) {
-                    x = net_member(P, q, i0 + lane);
-                    const int cx = P.col[x];
-                    c = cx < 0 ? -cx : 0;
-                    if (c) d = __ldg(P.deg + x);
-                }
-                const uint64_t hx = c ? prio_hash(seed, (uint32_t)x) : 0ull;
-                bool lose = false;
-                for (int j0 = 0; j0 < m; j0 += 32) {
-                    int y = -1, cy = 0, dy = 0;
-                    if (j0 + lane < m) {
-                        y = net_member(P, q, j0 + lane);
-                        const int c2 = P.col[y];
-                        cy = c2 < 0 ? -c2 : 0;
-                        if (cy) dy = __ldg(P.deg + y);
-                    }
-                    unsigned cand = __ballot_sync(kFullMask, cy != 0);
-                    while (cand) {
-                        const int src = __ffs(cand) - 1;
-                        cand &= cand - 1;
-                        const int ys = __shfl_sync(kFullMask, y, src);
-                        const int cs = __shfl_sync(kFullMask, cy, src);
-                        const int ds = __shfl_sync(kFullMask, dy, src);
-                        if (c && cs == c && ys != x && higher(ds, ys, d, hx, x, seed, use_deg))
-                            lose = true;
-                    }
-                }
-                if (lose) P.lose[x] = 1;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+        int x = -1, c = 0, d = 0;
+        uint64_t hx = 0ull;
+        if (i0 + lane < m) {
+            x = net_member(P, q, i0 + lane);
+            const int cx = P.col[x];
+            c = cx < 0 ? -cx : 0;
+            if (c) {
+                d = __ldg(P.deg + x);
+                hx = prio_hash(seed, (uint32_t)x);
             }
         }
-      }
+        bool lose = false;
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            // members of chunk j0 broadcast (id, color, degree, hash)
+            int y = -1, cy = 0, dy = 0;
+            uint64_t hy = 0ull;
+            if (j0 + lane < m) {
+                y = net_member(P, q, j0 + lane);
+                const int c2 = P.col[y];
+                cy = c2 < 0 ? -c2 : 0;
+                if (cy) {
+                    dy = __ldg(P.deg + y);
+                    hy = prio_hash(seed, (uint32_t)y);
+                }
+            }
+            unsigned cand = __ballot_sync(kFullMask, cy != 0);
+            while (cand) {
+                const int src = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int ys = __shfl_sync(kFullMask, y, src);
+                const int cs = __shfl_sync(kFullMask, cy, src);
+                const int ds = __shfl_sync(kFullMask, dy, src);
+                const uint64_t hs = __shfl_sync(kFullMask, hy, src);
+                if (c && cs == c && ys != x && has_priority(ds, hs, ys, d, hx, x, use_deg))
+                    lose = true;
+            }
+        }
+        if (lose) P.lose[x] = 1;
+    }
+}
+
+__global__ void net_detect(const Problem* __restrict__ Pp) {
+    // per warp: the tile's small active nets, compacted (net id, m_ptr,
+    // start of the net in the packed tile)
+    extern __shared__ int det_smem[];
+    const Problem& P = *Pp;
+    const int r = *(volatile int*)&P.st->round;
+    const bool all = *(volatile int*)&P.st->all_active != 0;
+    const int lane = lane_id(), wpb = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const unsigned long long seed = P.seed;
+    const bool use_deg = P.use_deg != 0;
+    const int self = P.self;
+    const int nn = P.n_nets;
+    int* sq = det_smem + w * kDetSmemInts;
+    int* sb = sq + 32;
+    int* sp = sb + 32;
+    for (long long b0 = ((long long)blockIdx.x * wpb + w) * 32; b0 < nn;
+         b0 += (long long)gridDim.x * wpb * 32) {
+        const int q = (int)b0 + lane;
+        int beg = 0, m = 0;
+        if (q < nn && (all || P.net_flag[q] == r)) {
+            beg = __ldg(P.m_ptr + q);
+            m = __ldg(P.m_ptr + q + 1) - beg + self;
+        }
+        const bool small = m >= 2 && m <= 32;
+        const unsigned sm = __ballot_sync(kFullMask, small);
+        const unsigned big = __ballot_sync(kFullMask, m > 32);
+        if (sm) {
+            // exclusive scan of the small nets' sizes = their packed starts
+            const int sz = small ? m : 0;
+            int e = sz;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFullMask, e, o);
+                if (lane >= o) e += t;
+            }
+            const int rank = __popc(sm & ((1u << lane) - 1u));
+            const int cnt = __popc(sm);
+            if (small) {
+                sq[rank] = q;
+                sb[rank] = beg;
+                sp[rank] = e - sz;
+            }
+            if (lane == 31) sp[cnt] = e;
+            __syncwarp();
+            // compacted net `lane`: its packed start and end
+            const int cS = lane < cnt ? sp[lane] : 0x7fffffff;
+            const int cE = lane < cnt ? sp[lane + 1] : 0x7fffffff;
+            int r0 = 0;
+            while (r0 < cnt) {
+                int x[kDetRows], cx[kDetRows], dx[kDetRows], id[kDetRows];
+#pragma unroll
+                for (int k = 0; k < kDetRows; ++k) {
+                    x[k] = -1;
+                    id[k] = 0;
+                    if (r0 >= cnt) continue;   // warp-uniform
+                    // the row: nets r0..r1-1, all that end within 32 lanes
+                    const int base = __shfl_sync(kFullMask, cS, r0);
+                    const unsigned fits = __ballot_sync(kFullMask, lane >= r0 && cE <= base + 32);
+                    const int r1 = 32 - __clz(fits);
+                    const unsigned starts = __reduce_or_sync(
+                        kFullMask, (lane >= r0 && lane < r1) ? 1u << (cS - base) : 0u);
+                    const int len = __shfl_sync(kFullMask, cE, r1 - 1) - base;
+                    if (lane < len) {
+                        const int i = r0 + __popc(starts & lanemask_le()) - 1;
+                        const int off = base + lane - sp[i];
+                        const int qq = sq[i], bg = sb[i];
+                        id[k] = i - r0 + 1;
+                        x[k] = self ? (off == 0 ? qq : __ldg(P.m_idx + bg + off - 1))
+                                    : __ldg(P.m_idx + bg + off);
+                    }
+                    r0 = r1;
+                }
+#pragma unroll
+                for (int k = 0; k < kDetRows; ++k) {
+                    cx[k] = 0;
+                    dx[k] = 0;
+                    if (x[k] >= 0) {
+                        cx[k] = P.col[x[k]];
+                        dx[k] = __ldg(P.deg + x[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kDetRows; ++k) {
+                    // only uncolored members can conflict
+                    const int c = cx[k] < 0 ? -cx[k] : 0;
+                    const unsigned key = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
+                    const unsigned g = __match_any_sync(kFullMask, key);
+                    if (c && __popc(g) > 1 && group_loses(g, x[k], dx[k], seed, use_deg))
+                        P.lose[x[k]] = 1;
+                }
+            }
+        }
+        // nets of more than 32 members, one at a time
+        unsigned bg = big;
+        while (bg) {
+            const int src = __ffs(bg) - 1;
+            bg &= bg - 1;
+            const int qb = __shfl_sync(kFullMask, q, src);
+            const int mb = __shfl_sync(kFullMask, m, src);
+            big_net_detect(P, qb, mb, lane);
+        }
+        __syncwarp();
     }
 }
 
@@ -336,6 +447,8 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
         status = ST_TIMEOUT;
     }
     if (!done) {
+        // when the next worklist touches about every net, skip the marking
+        st->all_active = *(volatile unsigned long long*)&st->h_next >= 2ull * (unsigned long long)P.n_nets;
         st->nt[cp] = st->nw[cp] = 0;
         st->round = r + 1;
         st->s_next = 0ull;
@@ -478,16 +591,18 @@ static Context* get_context(int device) {
 
 struct Geometry {
     int grid, block;
-    size_t smem;
+    size_t smem;       // init and commit
+    size_t det_smem;   // detect
 };
 
 static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
     g->block = o.block;
     g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
+    g->det_smem = (size_t)(o.block / 32) * kDetSmemInts * sizeof(int);
     int per_sm = o.grid_per_sm;
     if (per_sm == 0) {
         int a = 0, b = 0;
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, net_detect, o.block, 0));
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, net_detect, o.block, g->det_smem));
         PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, net_commit, o.block, g->smem));
         per_sm = std::max(1, std::min(a, b));
     }
@@ -524,7 +639,7 @@ static pgc_status build_graph(Context& cx, const Geometry& g) {
     PGC_CUDA(cudaGraphAddNode(&n_loop, cx.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaKernelNodeParams k_asg = knode((void*)net_assign, g, 0, c_args);
-    cudaKernelNodeParams k_det = knode((void*)net_detect, g, 0, p_args);
+    cudaKernelNodeParams k_det = knode((void*)net_detect, g, g.det_smem, p_args);
     cudaKernelNodeParams k_com = knode((void*)net_commit, g, g.smem, c_args);
     cudaGraphNode_t b_asg, b_det, b_com;
     PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
@@ -628,7 +743,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
             PGC_CUDA(cudaGetLastError());
             if (pgc_status s = kt.end()) return s;
             if (pgc_status s = kt.begin(2, "net_detect")) return s;
-            net_detect<<<g.grid, g.block, 0, stream>>>(dP);
+            net_detect<<<g.grid, g.block, g.det_smem, stream>>>(dP);
             PGC_CUDA(cudaGetLastError());
             if (pgc_status s = kt.end()) return s;
             if (pgc_status s = kt.begin(3, "net_commit")) return s;
