@@ -64,7 +64,7 @@ struct Problem {
     const int* r_ptr;     // vertex -> nets
     const int* r_idx;
     int* col;
-    int* deg;
+    unsigned long long* key;    // priority key (see net_init)
     int* lose;
     int* net_flag;              // = round number while the net is active
     unsigned long long* mask;   // [window][net]
@@ -100,7 +100,13 @@ __device__ __forceinline__ int vertex_net(const Problem& P, int v, int beg, int 
 }
 
 // ---------------------------------------------------------------------------
-// init: degrees, empty colors, worklists by number of nets, the color bound
+// init: priority keys, empty colors, worklists by number of nets, the bound
+//
+// key(v) = deg(v) << 32 | ~(h(v) >> 32) (deg term 0 without the degree
+// rule): a larger key is a higher priority (Alg. 4: larger degree first,
+// then the smaller hash), except between two keys that are equal -- same
+// degree and same top 32 hash bits -- which the low hash bits and then the
+// id decide.
 // ---------------------------------------------------------------------------
 __global__ void net_init(const Problem* __restrict__ Pp) {
     extern __shared__ int smem[];
@@ -120,7 +126,8 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
             const int v = (int)i;
             const int beg = __ldg(P.r_ptr + v);
             const int d = __ldg(P.r_ptr + v + 1) - beg;
-            P.deg[v] = d;
+            const unsigned hi = (unsigned)(prio_hash(P.seed, (uint32_t)v) >> 32);
+            P.key[v] = (P.use_deg ? (unsigned long long)d << 32 : 0ull) | (unsigned long long)~hi;
             P.col[v] = 0;
             P.lose[v] = 0;
             k = d + P.self;
@@ -242,57 +249,57 @@ __device__ __forceinline__ unsigned lanemask_le() {
 
 // g: the lanes (this one included) holding this lane's tentative color in
 // the same net.  True if one of them has priority over this lane's x.
-__device__ __forceinline__ bool group_loses(unsigned g, int x, int d, unsigned long long seed,
-                                            bool use_deg) {
-    if (use_deg) {
-        const unsigned md = __reduce_max_sync(g, (unsigned)d);
-        const unsigned g2 = __ballot_sync(g, (unsigned)d == md) & g;
-        if ((unsigned)d != md) return true;
-        g = g2;
-        if (__popc(g) == 1) return false;
-    }
-    const uint64_t h = prio_hash(seed, (uint32_t)x);
-    const unsigned hi = (unsigned)(h >> 32), lo = (unsigned)h;
-    const unsigned mh = __reduce_min_sync(g, hi);
-    const unsigned g3 = __ballot_sync(g, hi == mh) & g;
-    if (hi != mh) return true;
+__device__ __forceinline__ bool group_loses(unsigned g, int x, unsigned long long k,
+                                            unsigned long long seed) {
+    const unsigned khi = (unsigned)(k >> 32), klo = (unsigned)k;
+    const unsigned m1 = __reduce_max_sync(g, khi);
+    const unsigned g1 = __ballot_sync(g, khi == m1) & g;
+    if (khi != m1) return true;
+    if (__popc(g1) == 1) return false;
+    const unsigned m2 = __reduce_max_sync(g1, klo);
+    const unsigned g2 = __ballot_sync(g1, klo == m2) & g1;
+    if (klo != m2) return true;
+    if (__popc(g2) == 1) return false;
+    // equal keys: the low hash bits, then the id (equal ids: the same
+    // vertex listed twice)
+    const unsigned lo = (unsigned)prio_hash(seed, (uint32_t)x);
+    const unsigned m3 = __reduce_min_sync(g2, lo);
+    const unsigned g3 = __ballot_sync(g2, lo == m3) & g2;
+    if (lo != m3) return true;
     if (__popc(g3) == 1) return false;
-    const unsigned ml = __reduce_min_sync(g3, lo);
-    const unsigned g4 = __ballot_sync(g3, lo == ml) & g3;
-    if (lo != ml) return true;
-    if (__popc(g4) == 1) return false;
-    // equal keys: the same vertex listed twice, or the smaller id wins
-    return (unsigned)x != __reduce_min_sync(g4, (unsigned)x);
+    return (unsigned)x != __reduce_min_sync(g3, (unsigned)x);
+}
+
+// True if u has priority over v, from their keys (ties: full hash, then id).
+__device__ __forceinline__ bool key_priority(unsigned long long ku, int u, unsigned long long kv,
+                                             int v, unsigned long long seed) {
+    if (ku != kv) return ku > kv;
+    const uint64_t hu = prio_hash(seed, (uint32_t)u), hv = prio_hash(seed, (uint32_t)v);
+    if (hu != hv) return hu < hv;
+    return u < v;
 }
 
 __device__ void big_net_detect(const Problem& P, int q, int m, int lane) {
     const unsigned long long seed = P.seed;
-    const bool use_deg = P.use_deg != 0;
     for (int i0 = 0; i0 < m; i0 += 32) {
-        int x = -1, c = 0, d = 0;
-        uint64_t hx = 0ull;
+        int x = -1, c = 0;
+        unsigned long long kx = 0ull;
         if (i0 + lane < m) {
             x = net_member(P, q, i0 + lane);
             const int cx = P.col[x];
             c = cx < 0 ? -cx : 0;
-            if (c) {
-                d = __ldg(P.deg + x);
-                hx = prio_hash(seed, (uint32_t)x);
-            }
+            if (c) kx = __ldg(P.key + x);
         }
         bool lose = false;
         for (int j0 = 0; j0 < m; j0 += 32) {
-            // members of chunk j0 broadcast (id, color, degree, hash)
-            int y = -1, cy = 0, dy = 0;
-            uint64_t hy = 0ull;
+            // members of chunk j0 broadcast (id, color, key)
+            int y = -1, cy = 0;
+            unsigned long long ky = 0ull;
             if (j0 + lane < m) {
                 y = net_member(P, q, j0 + lane);
                 const int c2 = P.col[y];
                 cy = c2 < 0 ? -c2 : 0;
-                if (cy) {
-                    dy = __ldg(P.deg + y);
-                    hy = prio_hash(seed, (uint32_t)y);
-                }
+                if (cy) ky = __ldg(P.key + y);
             }
             unsigned cand = __ballot_sync(kFullMask, cy != 0);
             while (cand) {
@@ -300,13 +307,36 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane) {
                 cand &= cand - 1;
                 const int ys = __shfl_sync(kFullMask, y, src);
                 const int cs = __shfl_sync(kFullMask, cy, src);
-                const int ds = __shfl_sync(kFullMask, dy, src);
-                const uint64_t hs = __shfl_sync(kFullMask, hy, src);
-                if (c && cs == c && ys != x && has_priority(ds, hs, ys, d, hx, x, use_deg))
-                    lose = true;
+                const unsigned long long ks = __shfl_sync(kFullMask, ky, src);
+                if (c && cs == c && ys != x && key_priority(ks, ys, kx, x, seed)) lose = true;
             }
         }
         if (lose) P.lose[x] = 1;
+    }
+}
+
+// Loads the colors and keys of up to kDetRows rows of members (x < 0: no
+// member) and flags the losers.  id: 1 + the net's index within its row.
+__device__ __forceinline__ void resolve_rows(const Problem& P, const int (&x)[kDetRows],
+                                             const int (&id)[kDetRows], unsigned long long seed) {
+    int cx[kDetRows];
+    unsigned long long kx[kDetRows];
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) {
+        cx[k] = 0;
+        kx[k] = 0ull;
+        if (x[k] >= 0) {
+            cx[k] = P.col[x[k]];
+            kx[k] = __ldg(P.key + x[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) {
+        // only uncolored members can conflict
+        const int c = cx[k] < 0 ? -cx[k] : 0;
+        const unsigned tag = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
+        const unsigned g = __match_any_sync(kFullMask, tag);
+        if (c && __popc(g) > 1 && group_loses(g, x[k], kx[k], seed)) P.lose[x[k]] = 1;
     }
 }
 
@@ -319,7 +349,6 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
     const bool all = *(volatile int*)&P.st->all_active != 0;
     const int lane = lane_id(), wpb = blockDim.x >> 5, w = threadIdx.x >> 5;
     const unsigned long long seed = P.seed;
-    const bool use_deg = P.use_deg != 0;
     const int self = P.self;
     const int nn = P.n_nets;
     int* sq = det_smem + w * kDetSmemInts;
@@ -336,7 +365,30 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
         const bool small = m >= 2 && m <= 32;
         const unsigned sm = __ballot_sync(kFullMask, small);
         const unsigned big = __ballot_sync(kFullMask, m > 32);
-        if (sm) {
+        if (sm && __reduce_min_sync(kFullMask, small ? m : 64) > 16) {
+            // every row holds exactly one net
+            unsigned rest = sm;
+            while (rest) {
+                int x[kDetRows], id[kDetRows];
+#pragma unroll
+                for (int k = 0; k < kDetRows; ++k) {
+                    x[k] = -1;
+                    id[k] = 0;
+                    if (!rest) continue;   // warp-uniform
+                    const int src = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const int qq = __shfl_sync(kFullMask, q, src);
+                    const int bg = __shfl_sync(kFullMask, beg, src);
+                    const int mm = __shfl_sync(kFullMask, m, src);
+                    if (lane < mm) {
+                        id[k] = 1;
+                        x[k] = self ? (lane == 0 ? qq : __ldg(P.m_idx + bg + lane - 1))
+                                    : __ldg(P.m_idx + bg + lane);
+                    }
+                }
+                resolve_rows(P, x, id, seed);
+            }
+        } else if (sm) {
             // exclusive scan of the small nets' sizes = their packed starts
             const int sz = small ? m : 0;
             int e = sz;
@@ -359,7 +411,7 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
             const int cE = lane < cnt ? sp[lane + 1] : 0x7fffffff;
             int r0 = 0;
             while (r0 < cnt) {
-                int x[kDetRows], cx[kDetRows], dx[kDetRows], id[kDetRows];
+                int x[kDetRows], id[kDetRows];
 #pragma unroll
                 for (int k = 0; k < kDetRows; ++k) {
                     x[k] = -1;
@@ -382,24 +434,7 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
                     }
                     r0 = r1;
                 }
-#pragma unroll
-                for (int k = 0; k < kDetRows; ++k) {
-                    cx[k] = 0;
-                    dx[k] = 0;
-                    if (x[k] >= 0) {
-                        cx[k] = P.col[x[k]];
-                        dx[k] = __ldg(P.deg + x[k]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kDetRows; ++k) {
-                    // only uncolored members can conflict
-                    const int c = cx[k] < 0 ? -cx[k] : 0;
-                    const unsigned key = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
-                    const unsigned g = __match_any_sync(kFullMask, key);
-                    if (c && __popc(g) > 1 && group_loses(g, x[k], dx[k], seed, use_deg))
-                        P.lose[x[k]] = 1;
-                }
+                resolve_rows(P, x, id, seed);
             }
         }
         // nets of more than 32 members, one at a time
@@ -533,13 +568,13 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf deg, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col;
+    DevBuf key, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
-    int g_grid = 0, g_block = 0;
+    int g_grid = 0, g_block = 0, g_det = 0;
 
     void destroy_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -550,7 +585,7 @@ struct Context {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&deg, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
+        for (DevBuf* b : {&key, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
                           &stage_col, &stage[0], &stage[1], &stage[2], &stage[3]})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
@@ -591,6 +626,7 @@ static Context* get_context(int device) {
 
 struct Geometry {
     int grid, block;
+    int det_grid;      // detect (its own occupancy)
     size_t smem;       // init and commit
     size_t det_smem;   // detect
 };
@@ -605,6 +641,9 @@ static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
         PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, net_detect, o.block, g->det_smem));
         PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, net_commit, o.block, g->smem));
         per_sm = std::max(1, std::min(a, b));
+        g->det_grid = cx.dev.num_sms * std::max(1, a);
+    } else {
+        g->det_grid = cx.dev.num_sms * per_sm;
     }
     g->grid = cx.dev.num_sms * per_sm;
     return PGC_OK;
@@ -640,6 +679,7 @@ static pgc_status build_graph(Context& cx, const Geometry& g) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaKernelNodeParams k_asg = knode((void*)net_assign, g, 0, c_args);
     cudaKernelNodeParams k_det = knode((void*)net_detect, g, g.det_smem, p_args);
+    k_det.gridDim = dim3(g.det_grid);
     cudaKernelNodeParams k_com = knode((void*)net_commit, g, g.smem, c_args);
     cudaGraphNode_t b_asg, b_det, b_com;
     PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
@@ -647,6 +687,7 @@ static pgc_status build_graph(Context& cx, const Geometry& g) {
     PGC_CUDA(cudaGraphAddKernelNode(&b_com, body, &b_det, 1, &k_com));
     PGC_CUDA(cudaGraphInstantiate(&cx.exec, cx.graph, 0));
     cx.g_grid = g.grid;
+    cx.g_det = g.det_grid;
     cx.g_block = g.block;
     return PGC_OK;
 }
@@ -660,7 +701,7 @@ struct Input {
 static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o,
                       cudaStream_t stream, int* rounds, int* num_colors) {
     const int n = in.n;
-    if (pgc_status s = cx.deg.ensure((size_t)n * 4)) return s;
+    if (pgc_status s = cx.key.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.lose.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.flag.ensure((size_t)std::max(in.n_nets, 1) * 4)) return s;
     if (pgc_status s = cx.wt.ensure((size_t)n * 4 * 2)) return s;
@@ -686,7 +727,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     hp->r_ptr = in.r_ptr;
     hp->r_idx = in.r_idx;
     hp->col = in.col;
-    hp->deg = cx.deg.as<int>();
+    hp->key = cx.key.as<unsigned long long>();
     hp->lose = cx.lose.as<int>();
     hp->net_flag = cx.flag.as<int>();
     for (int p = 0; p < 2; ++p) {
@@ -731,7 +772,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     PGC_CUDA(cudaMemsetAsync(cx.mask.ptr, 0, mask_bytes, stream));
 
     if (!(o.flags & PGC_HOST_LOOP)) {
-        if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block) {
+        if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block || cx.g_det != g.det_grid) {
             if (pgc_status s = build_graph(cx, g)) return s;
         }
         PGC_CUDA(cudaGraphLaunch(cx.exec, stream));
@@ -743,7 +784,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
             PGC_CUDA(cudaGetLastError());
             if (pgc_status s = kt.end()) return s;
             if (pgc_status s = kt.begin(2, "net_detect")) return s;
-            net_detect<<<g.grid, g.block, g.det_smem, stream>>>(dP);
+            net_detect<<<g.det_grid, g.block, g.det_smem, stream>>>(dP);
             PGC_CUDA(cudaGetLastError());
             if (pgc_status s = kt.end()) return s;
             if (pgc_status s = kt.begin(3, "net_commit")) return s;
@@ -795,7 +836,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
 // ---------------------------------------------------------------------------
 size_t scratch_bytes(int n, int n_nets, int windows) {
     auto a = [](size_t x) { return (x + 255) / 256 * 256; };
-    return a((size_t)n * 4) * 2 + a((size_t)std::max(n_nets, 1) * 4) +
+    return a((size_t)n * 8) + a((size_t)n * 4) + a((size_t)std::max(n_nets, 1) * 4) +
            a((size_t)windows * (size_t)std::max(n_nets, 1) * 8) + a((size_t)n * 8) * 2;
 }
 
@@ -804,8 +845,8 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     const int n = in.n;
     auto a = [](size_t x) { return (x + 255) / 256 * 256; };
     char* p = static_cast<char*>(scratch);
-    int* deg = reinterpret_cast<int*>(p);
-    p += a((size_t)n * 4);
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(p);
+    p += a((size_t)n * 8);
     int* lose = reinterpret_cast<int*>(p);
     p += a((size_t)n * 4);
     int* flag = reinterpret_cast<int*>(p);
@@ -830,7 +871,7 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     hp->r_ptr = in.r_ptr;
     hp->r_idx = in.r_idx;
     hp->col = in.col;
-    hp->deg = deg;
+    hp->key = key;
     hp->lose = lose;
     hp->net_flag = flag;
     hp->mask = mask;
@@ -855,7 +896,7 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     PGC_CUDA(cudaMemsetAsync(mask, 0, mask_bytes, stream));
     net_init<<<g.grid, g.block, g.smem, stream>>>(dP);
     PGC_CUDA(cudaGetLastError());
-    if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block) {
+    if (!cx.exec || cx.g_grid != g.grid || cx.g_block != g.block || cx.g_det != g.det_grid) {
         if (pgc_status s = build_graph(cx, g)) return s;
     }
     PGC_CUDA(cudaGraphLaunch(cx.exec, stream));
