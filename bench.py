@@ -142,6 +142,29 @@ def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None):
     return out
 
 
+def d1_method_bytes(trace_w, trace_s, n, nnz, tail_at=None):
+    """Bytes the method's conflict detection must move per round, as the
+    method states it (every worklist vertex reads its whole adjacency and
+    its neighbors' colors; int32 everywhere), for the rounds run by the
+    per-round detect launches:
+      round 1:   offsets 4(n+1) + adjacency 4 nnz + neighbor degrees 4 nnz +
+                 colors 4n + next worklist 4|W_2|
+      round r:   worklist 4|W_r| + offsets 8|W_r| + adjacency 4 S_r +
+                 neighbor colors 4 S_r + color write 4|W_r| + next worklist
+                 4|W_{r+1}|  (degree gathers of equal-colored neighbors,
+                 4 T_r, are not counted: T_r is not traced)
+    Returns (total bytes, rounds counted)."""
+    w = np.asarray(trace_w, dtype=np.float64)
+    sw = np.asarray(trace_s, dtype=np.float64)
+    R = len(w)
+    t = R if tail_at is None else tail_at
+    wn = np.append(w[1:], 0.0)
+    per = 16 * w + 8 * sw + 4 * wn
+    if R:
+        per[0] = 4.0 * (n + 1) + 8.0 * nnz + 4.0 * n + 4 * wn[0]
+    return float(per[:t].sum()), t
+
+
 # --------------------------------------------------------------------------
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -380,10 +403,10 @@ def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, slots, seed=7)
             "budget_bytes": budget, "identical_colors": bool(same)}
 
 
-def bench_net(pgc, inputs, torch, dev, reps=5):
+def bench_net(pgc, inputs, torch, dev, reps=5, warm=2, flags=0, timeout_ms=0):
     """Distance-2 on the 27-point stencil 128^3 and partial distance-2 on the
-    4M x 1M pattern (config 3), inputs resident; edges = nnz/2 for D2 (a
-    symmetric graph) and nnz for PD2 (row-column entries)."""
+    4M x 1M pattern, inputs resident; edges = nnz/2 for D2 (a symmetric
+    graph) and nnz for PD2 (row-column entries)."""
     out = {}
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -391,12 +414,14 @@ def bench_net(pgc, inputs, torch, dev, reps=5):
     g = inputs.stencil3d(128, 128, 128, points=27)
     rp, ci = t(g.row_ptr), t(g.col_idx)
     col = torch.empty(g.n, dtype=torch.int32, device=dev)
-    for _ in range(2):
-        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream)
+    for _ in range(warm):
+        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream, flags=flags,
+                             timeout_ms=timeout_ms)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     for _ in range(reps):
-        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream)
+        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream, flags=flags,
+                             timeout_ms=timeout_ms)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / reps
@@ -407,12 +432,14 @@ def bench_net(pgc, inputs, torch, dev, reps=5):
     b = inputs.bipartite(1 << 22, 1 << 20, seed=SEED)
     a = [t(x) for x in (b.row_ptr, b.col_idx, b.col_ptr, b.row_idx)]
     col = torch.empty(b.n_cols, dtype=torch.int32, device=dev)
-    for _ in range(2):
-        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream)
+    for _ in range(warm):
+        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream,
+                              flags=flags, timeout_ms=timeout_ms)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     for _ in range(reps):
-        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream)
+        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream,
+                              flags=flags, timeout_ms=timeout_ms)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / reps
@@ -452,6 +479,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--net-only", action="store_true",
+                    help="time only the distance-2 and partial distance-2 configurations "
+                         "(--warmup and --steps calls each, round loop per --loop)")
     ap.add_argument("--dump-profile", default=None,
                     help="write per-launch times and the per-round trace to this JSON file")
     args = ap.parse_args()
@@ -478,6 +508,16 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.net_only:
+        if rank == 0:
+            flags = pgc.PGC_HOST_LOOP if args.loop == "host" else 0
+            print(json.dumps(bench_net(pgc, inputs, torch, dev, reps=args.steps,
+                                       warm=args.warmup, flags=flags,
+                                       timeout_ms=args.timeout_ms)), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # ---- input (identical on every replica) ----
     t0 = time.time()
@@ -568,7 +608,14 @@ def main():
         top = max(prof.kernel_ms, key=prof.kernel_ms.get)
         launches = prof.kernel_launches[top]
         avg_s = prof.kernel_ms[top] / 1000.0 / launches
+        # bytes this design must move (priority lists, pushed forbidden
+        # sets); the method's own per-round adjacency scan is reported beside
+        # it for context -- this design does not move those bytes
         per_launch = nbytes[top] / launches
+        method_per_launch = None
+        if top == "d1_detect":
+            tot, _ = d1_method_bytes(prof.trace_w, prof.trace_s, n, nnz, tail_at)
+            method_per_launch = tot / launches
         achieved = per_launch / avg_s / 1e9
         # DRAM bytes per launch from an ncu capture (profiles/traffic.json),
         # used only while the kernel source is the one that was measured
@@ -586,7 +633,10 @@ def main():
                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                     "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
                     "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1000,
-                    "launches": launches}
+                    "launches": launches,
+                    "method_bytes_per_launch": method_per_launch,
+                    "method_rate_gbs": (method_per_launch / avg_s / 1e9
+                                        if method_per_launch else None)}
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None

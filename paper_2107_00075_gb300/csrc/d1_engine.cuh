@@ -197,9 +197,7 @@ __device__ __forceinline__ long long bm_offset(long long row_begin, int v) {
 // colored vertex is harmless (its set is never read again), so colors 1..64
 // need no check and the update is a fire-and-forget reduction.
 template <class V>
-__device__ __forceinline__ void push_color(const Problem<V>& P, int u, int g, int c) {
-    // most neighbors of a late winner are colored already: skip them
-    if (!((P.live[u >> 5] >> (u & 31)) & 1u)) return;
+__device__ __forceinline__ void push_color_live(const Problem<V>& P, int u, int g, int c) {
     if (c <= 64) {
         atomicOr(P.bm0 + u, 1ull << (c - 1));
         return;
@@ -210,6 +208,11 @@ __device__ __forceinline__ void push_color(const Problem<V>& P, int u, int g, in
     if (c - 1 > du) return;   // u's own first fit never reaches c
     const int b = c - 65;
     atomicOr(P.bmx + bm_offset(bu, u) + (b >> 5), 1u << (b & 31));
+}
+template <class V>
+__device__ __forceinline__ void push_color(const Problem<V>& P, int u, int g, int c) {
+    // most neighbors of a late winner are colored already: skip them
+    if ((P.live[u >> 5] >> (u & 31)) & 1u) push_color_live(P, u, g, c);
 }
 
 // Batch bookkeeping: arr[g] = max(arr[g], val) over the lanes with pred,
@@ -528,14 +531,15 @@ __device__ __forceinline__ void queue_push(const Problem<V>& P, int v, int d) {
     for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
 }
 
-// Warp-wide: does any of the H-list entries [0, hl) of v (starting at
+// Warp-wide: does any of the H-list entries [from, hl) of v (starting at
 // hadj[beg]) currently hold color t?  32 entries per step; the ids of the
 // next step are loaded before this step's colors are compared.
 template <class V>
-__device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg, int hl, int t) {
+__device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg, int hl, int t,
+                                              int from) {
     const int lane = lane_id();
-    int nxt = lane < hl ? __ldg(P.hadj + beg + lane) : -1;
-    for (int b0 = 0; b0 < hl; b0 += 32) {
+    int nxt = from + lane < hl ? __ldg(P.hadj + beg + from + lane) : -1;
+    for (int b0 = from; b0 < hl; b0 += 32) {
         const int u = nxt;
         const int e = b0 + 32 + lane;
         nxt = e < hl ? __ldg(P.hadj + beg + e) : -1;
@@ -598,14 +602,34 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
         __syncthreads();
     }
 
-    // --- M tier: one warp per vertex ---
+    // --- M tier: one warp per vertex.  The next vertex's entry is loaded
+    // while this one's first 32 list colors are gathered, and its own color
+    // and first 32 list ids while this one is committed or appended. ---
+    int4 ent = make_int4(-1, 0, 0, 0);
+    long long beg = 0;
+    int g = 0, t = 0, u0 = -1;
+    if (gw < nM) {
+        ent = P.wm[cp][gw];
+        g = P.g.graph(ent.x);
+        beg = P.g.begin(g, ent.w);
+        t = -col[ent.x];
+        u0 = lane < ent.y ? __ldg(ha + beg + lane) : -1;
+    }
     for (int i = gw; i < nM; i += nw) {
-        const int4 ent = P.wm[cp][i];
         const int v = ent.x, hl = ent.y, d = ent.z;
-        const int g = P.g.graph(v);
-        const long long beg = P.g.begin(g, ent.w);
-        const int t = -col[v];
-        const bool lose = warp_conflict(P, beg, hl, t);
+        const int in = i + nw;
+        int4 en = make_int4(-1, 0, 0, 0);
+        if (in < nM) en = P.wm[cp][in];
+        bool lose = __any_sync(kFullMask, u0 >= 0 && abs(col[u0]) == t);
+        if (!lose && hl > 32) lose = warp_conflict(P, beg, hl, t, 32);
+        int gn = 0, tn = 0, un = -1;
+        long long bn = 0;
+        if (in < nM) {
+            gn = P.g.graph(en.x);
+            bn = P.g.begin(gn, en.w);
+            tn = -col[en.x];
+            un = lane < en.y ? __ldg(ha + bn + lane) : -1;
+        }
         if (lane == 0) {
             if (lose) {
                 my_s += (unsigned long long)d;
@@ -620,6 +644,11 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             }
         }
         tier_push(P, app, lose && lane == 0, ent, np);
+        ent = en;
+        beg = bn;
+        g = gn;
+        t = tn;
+        u0 = un;
     }
 
     // --- S tier: one thread per vertex ---
@@ -654,10 +683,20 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 atomicAnd(P.live + (v >> 5), ~(1u << (v & 31)));
                 my_max = max(my_max, t);
                 if (d <= kInlinePush) {
+                    // four neighbors at a time: ids, then their uncolored
+                    // bits, then the updates
                     const int base = P.g.base(g);
-                    for (int e = 0; e < d; ++e) {
-                        const int u = P.g.nbr(beg + e, base);
-                        if (u != v) push_color(P, u, g, t);
+                    for (int e0 = 0; e0 < d; e0 += 4) {
+                        int u[4];
+                        unsigned lw[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            u[j] = e0 + j < d ? P.g.nbr(beg + e0 + j, base) : v;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) lw[j] = u[j] != v ? P.live[u[j] >> 5] : 0u;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if ((lw[j] >> (u[j] & 31)) & 1u) push_color_live(P, u[j], g, t);
                     }
                 } else {
                     queue_push(P, v, d);
@@ -883,7 +922,7 @@ struct Engine {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
-    int g_grid = 0, g_block = 0;
+    int g_grid = 0, g_block = 0, g_det = 0;
 
     void destroy_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -905,6 +944,7 @@ struct Engine {
         int grid, block;
         size_t smem;   // two warp appenders per warp
         int tail_grid; // co-resident blocks for the cooperative tail kernel
+        int det_grid;  // detect: its own occupancy
     };
 
     pgc_status geometry(const Opts& o, Geometry* g) {
@@ -917,11 +957,13 @@ struct Engine {
                                               (int)g->smem));
         }
         int per_sm = o.grid_per_sm;
+        g->det_grid = dev.num_sms * per_sm;
         if (per_sm == 0) {
             int a = 0, b = 0;
             PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, d1_detect<V>, o.block, g->smem));
             PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, d1_build<V>, o.block, 0));
             per_sm = std::max(1, std::min(a, b));
+            g->det_grid = dev.num_sms * std::max(1, a);
         }
         g->grid = dev.num_sms * per_sm;
         int t = 0;
@@ -961,6 +1003,7 @@ struct Engine {
         cudaKernelNodeParams k_build = knode((void*)d1_build<V>, g, 0, p_args);
         cudaKernelNodeParams k_tier = knode((void*)d1_tier<V>, g, g.smem, p_args);
         cudaKernelNodeParams k_det = knode((void*)d1_detect<V>, g, g.smem, c_args);
+        k_det.gridDim = dim3(g.det_grid);
         cudaKernelNodeParams k_push = knode((void*)d1_push<V>, g, 0, p_args);
         cudaKernelNodeParams k_asg = knode((void*)d1_assign<V>, g, 0, c_args);
         PGC_CUDA(cudaGraphAddKernelNode(&n_cls, graph, &n_ms, 1, &k_cls));
@@ -989,6 +1032,7 @@ struct Engine {
         PGC_CUDA(cudaGraphKernelNodeSetAttribute(n_tail, cudaLaunchAttributeCooperative, &coop));
         PGC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         g_grid = g.grid;
+        g_det = g.det_grid;
         g_block = g.block;
         return PGC_OK;
     }
@@ -1093,7 +1137,7 @@ struct Engine {
 
         State* hs = h_state.as<State>();
         if (!(o.flags & PGC_HOST_LOOP)) {
-            if (!exec || g_grid != g.grid || g_block != g.block) {
+            if (!exec || g_grid != g.grid || g_block != g.block || g_det != g.det_grid) {
                 if (pgc_status s = build_graph(g)) return s;
             }
             PGC_CUDA(cudaGraphLaunch(exec, stream));
@@ -1118,7 +1162,7 @@ struct Engine {
                     PGC_TIMED(3, "d1_assign",
                               (d1_assign<V><<<g.grid, g.block, 0, stream>>>(dP, none, 0)));
                 PGC_TIMED(4, "d1_detect",
-                          (d1_detect<V><<<g.grid, g.block, g.smem, stream>>>(dP, none, 0)));
+                          (d1_detect<V><<<g.det_grid, g.block, g.smem, stream>>>(dP, none, 0)));
                 PGC_TIMED(5, "d1_push", (d1_push<V><<<g.grid, g.block, 0, stream>>>(dP)));
                 PGC_CUDA(cudaMemcpyAsync(hs, state.ptr, sizeof(State), cudaMemcpyDeviceToHost,
                                          stream));
