@@ -420,22 +420,50 @@ __global__ void d1_tier(const Problem<V>* __restrict__ Pp) {
 // ---------------------------------------------------------------------------
 // assign: first fit from the forbidden-color set
 // ---------------------------------------------------------------------------
+// First fit for worklist entry e = {v, |H(v)|, deg(v), local row start}.
+// The forbidden set only grows from round to round (committed colors are
+// final), so the first free color never decreases: the scan starts at the
+// previous round's tentative color, -col[v].
 template <class V>
-__device__ __forceinline__ void assign_one(const Problem<V>& P, int v) {
-    const unsigned long long w0 = P.bm0[v];
+__device__ __forceinline__ void assign_one(const Problem<V>& P, int4 e) {
+    const int v = e.x;
+    const int tp = -P.col[v];
     int t;
+    unsigned long long w0 = ~0ull;
+    if (tp <= 64) w0 = P.bm0[v];
     if (w0 != ~0ull) {
         t = __ffsll((long long)~w0);
     } else {   // colors 1..64 all taken: deg(v) >= 64, scan the overflow bitmap
-        long long b;
-        int d;
-        P.g.row(v, P.g.graph(v), b, d);
-        const int words = (d >> 5) + 1;
+        const int g = P.g.graph(v);
+        const long long b = P.g.begin(g, e.w);
+        const int words = (e.z >> 5) + 1;
         const unsigned* w = P.bmx + bm_offset(b, v);
-        int k = 0;
-        unsigned word = w[0];
-        while (word == kFullMask && k + 1 < words) word = w[++k];
-        t = 64 + k * 32 + __ffs(~word);
+        // four words per step, from the word that holds the previous color
+        int k = tp > 64 ? (tp - 65) >> 5 : 0;
+        for (;;) {
+            unsigned x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = k + j < words ? w[k + j] : 0u;
+            int j = 0;
+            unsigned y = x[0];
+            if (y == kFullMask) {
+                j = 1;
+                y = x[1];
+                if (y == kFullMask) {
+                    j = 2;
+                    y = x[2];
+                    if (y == kFullMask) {
+                        j = 3;
+                        y = x[3];
+                    }
+                }
+            }
+            if (y != kFullMask || k + 4 >= words) {
+                t = 64 + (k + j) * 32 + __ffs(~y);
+                break;
+            }
+            k += 4;
+        }
     }
     P.col[v] = -t;
 }
@@ -448,9 +476,9 @@ __device__ __forceinline__ void assign_phase(const Problem<V>& P) {
     const long long total = (long long)n0 + n1 + n2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int v = i < n0 ? P.ws[cp][i].x
-                    : (i < n0 + n1 ? P.wm[cp][i - n0].x : P.wl[cp][i - n0 - n1].x);
-        assign_one(P, v);
+        const int4 e = i < n0 ? P.ws[cp][i]
+                     : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
+        assign_one(P, e);
     }
 }
 
@@ -968,7 +996,9 @@ struct Engine {
         g->grid = dev.num_sms * per_sm;
         int t = 0;
         PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t, d1_tail<V>, o.block, g->smem));
-        g->tail_grid = dev.num_sms * std::max(1, std::min(t, std::max(per_sm, 1)));
+        // the tail's rounds are short and its phases meet at grid barriers:
+        // two blocks per SM keep those barriers cheap
+        g->tail_grid = dev.num_sms * std::max(1, std::min({t, std::max(per_sm, 1), 2}));
         return PGC_OK;
     }
 
