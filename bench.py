@@ -104,7 +104,8 @@ def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None):
     """Bytes each kernel must move for one coloring (int32 ids and colors,
     64-bit forbidden-color words), from the per-round trace: |W_r|,
     S_r = sum of deg over W_r and H_r = sum of |H(v)| over W_r (the scan
-    lists).  Rounds from tail_at on run inside the cooperative tail kernel.
+    lists).  Rounds from tail_at on run in the core phase (the subgraph
+    induced by the worklist), counted with the same per-round model.
       classify: offsets 4(n+1) + degree, color, list-length writes 12n +
                 forbidden word 8n + worklist 4n (overflow-bitmap clears of
                 vertices with deg >= 64 not counted)
@@ -138,7 +139,7 @@ def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None):
         "d1_push": float(psh[:t].sum()),
     }
     if t < R:
-        out["d1_tail"] = float(asg[t:].sum() + det[t:].sum() + psh[t:].sum())
+        out["d1_core"] = float(asg[t:].sum() + det[t:].sum() + psh[t:].sum())
     return out
 
 
@@ -661,13 +662,13 @@ def main():
 
     if rank == 0:
         # classify, build, tier, then (assign,) detect, push per round until the
-        # worklist is small, then one cooperative tail launch
+        # worklist is small, then the core phase (map, scan, fill, loop)
         tail_w = 4096 if args.tail_vertices == 0 else args.tail_vertices
         tail_at = None
         if trace_w is not None and tail_w > 0:
             tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
         loop_rounds = tail_at if tail_at is not None else rounds
-        launches_per_step = 3 + 3 * loop_rounds - 1 + (1 if tail_at is not None else 0)
+        launches_per_step = 3 + 3 * loop_rounds - 1 + (4 if tail_at is not None else 0)
         out = {
             "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

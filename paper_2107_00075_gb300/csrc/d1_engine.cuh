@@ -132,14 +132,19 @@ struct State {
     int push_cnt;     // push work items queued this round
     unsigned blocks_done;
     unsigned l_next;  // dynamic index into the L-tier worklist
-    int tail;         // 1: the graph loop handed the remaining rounds to d1_tail
-    unsigned bar_count;         // d1_tail grid barrier: arrivals
-    unsigned bar_gen;           // d1_tail grid barrier: generation
-    int bar_timeout;            // d1_tail: a barrier wait gave up
+    int tail;         // 1: the graph loop handed the remaining rounds to the core phase
+    unsigned bar_count;         // core loop grid barrier: arrivals
+    unsigned bar_gen;           // core loop grid barrier: generation
+    int bar_timeout;            // core loop: a barrier wait gave up
     unsigned long long s_next;  // sum of degrees of the next worklist
     unsigned long long h_next;  // sum of |H(v)| over the next worklist
     unsigned long long h_first; // sum of |H(v)| over all vertices
     unsigned long long t0;      // globaltimer at start
+    int core_k;       // core phase: vertices of the induced subgraph
+    int core_par;     // core phase: parity whose worklist buffers hold its arrays
+    int core_cur;     // core phase: size of the current local worklist
+    int core_nxt;     // core phase: appends to the next local worklist
+    int core_win;     // core phase: winners of the current round
 };
 
 template <class V>
@@ -174,7 +179,7 @@ struct Problem {
     int max_rounds;
     int det_s;
     int det_m;
-    int tail_w;        // hand over to d1_tail once the worklist is this small (0: never)
+    int tail_w;        // hand over to the core phase once the worklist is this small (0: never)
 };
 
 // key(u) > key(v) for u, v of the same graph (hash of graph-local ids),
@@ -425,9 +430,8 @@ __global__ void d1_tier(const Problem<V>* __restrict__ Pp) {
 // final), so the first free color never decreases: the scan starts at the
 // previous round's tentative color, -col[v].
 template <class V>
-__device__ __forceinline__ void assign_one(const Problem<V>& P, int4 e) {
+__device__ __forceinline__ int first_fit(const Problem<V>& P, int4 e, int tp) {
     const int v = e.x;
-    const int tp = -P.col[v];
     int t;
     unsigned long long w0 = ~0ull;
     if (tp <= 64) w0 = P.bm0[v];
@@ -465,7 +469,7 @@ __device__ __forceinline__ void assign_one(const Problem<V>& P, int4 e) {
             k += 4;
         }
     }
-    P.col[v] = -t;
+    return t;
 }
 
 template <class V>
@@ -478,7 +482,7 @@ __device__ __forceinline__ void assign_phase(const Problem<V>& P) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         const int4 e = i < n0 ? P.ws[cp][i]
                      : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
-        assign_one(P, e);
+        P.col[e.x] = -first_fit(P, e, -P.col[e.x]);
     }
 }
 
@@ -544,7 +548,7 @@ __device__ int round_decide(const Problem<V>& P) {
 
 // Round control of the launch-per-round loop: the WHILE node repeats while
 // the coloring is unfinished and the worklist is larger than tail_w; the
-// remaining rounds go to d1_tail.
+// remaining rounds go to the core phase.
 template <class V>
 __device__ void round_control(const Problem<V>& P, cudaGraphConditionalHandle h, int use_cond) {
     const int done = round_decide(P);
@@ -811,7 +815,7 @@ __global__ void d1_push(const Problem<V>* __restrict__ Pp) {
 }
 
 // ---------------------------------------------------------------------------
-// tail: the last, small rounds in one cooperative launch
+// grid barrier of the core loop
 // ---------------------------------------------------------------------------
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  A
 // wait that exceeds ~2^22 polls (about a second) gives up, records the
@@ -846,34 +850,436 @@ __device__ __forceinline__ bool grid_barrier(State* st) {
     return s_ok != 0;
 }
 
-// Runs assign / detect / push for every remaining round, with grid
-// barriers between the phases instead of kernel boundaries.  Entered when
-// the launch-per-round loop stopped with st->tail set; returns at once if
-// the coloring is already finished.
+// ---------------------------------------------------------------------------
+// core: the last rounds on the subgraph induced by the worklist
+// ---------------------------------------------------------------------------
+// Once the worklist W is small (at most tail_w vertices), the remaining
+// rounds only ever involve W: a vertex outside W is committed, so it can no
+// longer conflict (first fit avoids committed colors) and its forbidden set
+// is never read again.  The core phase therefore
+//   1. gives the vertices of W local ids and extracts, for each, its
+//      neighbors inside W -- the higher-priority ones first (the only ones
+//      Alg. 4 can make it lose to), then the others (which only receive its
+//      color when it commits);
+//   2. runs the rounds (assign, detect, push, round control) in one
+//      cooperative launch of a few 1024-thread blocks over these short
+//      local lists, with grid barriers between the phases;
+//   3. writes the colors back.
+// The rounds are the same rounds the per-round kernels would run (same
+// first fit on the same forbidden sets, same loser rule, same snapshot), so
+// colors, round count and trace are unchanged.
+//
+// Scratch: local id of v in hlen[v] (the list lengths are dead after
+// setup), induced lists in hadj (dead once the global lists are no longer
+// scanned; the induced lists are a subset of W's adjacency, so they fit),
+// per-vertex arrays in the other parity's worklist buffers (3 x 16n bytes).
+
+constexpr int kCoreBlocks = 32;     // blocks of the core loop (1024 threads each)
+constexpr int kCoreWarpDeg = 4096;  // rows up to this length: one warp; longer: one block
+
+struct CoreArrays {
+    int4* lent;   // [k] worklist entry {v, |H(v)|, deg, local row start}
+    int* vid;     // [k] global id
+    int* lhn;     // [k] number of higher-priority induced neighbors
+    int* lcol;    // [k] color (> 0 committed, -t tentative)
+    int* qwin;    // [k] winners of the round
+    int* loff;    // [k + 1] induced list offsets (higher ones first)
+    int* lw0;     // [k] local worklists (two sides)
+    int* lw1;
+};
+
 template <class V>
-__global__ void __maxnreg__(40) d1_tail(const Problem<V>* __restrict__ Pp) {
-    extern __shared__ int smem[];
+__device__ __forceinline__ CoreArrays core_arrays(const Problem<V>& P, int par, int k) {
+    CoreArrays a;
+    a.lent = P.ws[par];
+    int* m = reinterpret_cast<int*>(P.wm[par]);
+    a.vid = m;
+    a.lhn = m + k;
+    a.lcol = m + 2 * k;
+    a.qwin = m + 3 * k;
+    int* l = reinterpret_cast<int*>(P.wl[par]);
+    a.loff = l;
+    a.lw0 = l + k + 1;
+    a.lw1 = l + 2 * k + 1;
+    return a;
+}
+
+template <class V>
+__device__ __forceinline__ int4 core_entry(const Problem<V>& P, int cp, int nS, int nM, int i) {
+    return i < nS ? P.ws[cp][i] : (i < nS + nM ? P.wm[cp][i - nS] : P.wl[cp][i - nS - nM]);
+}
+
+__device__ __forceinline__ bool is_live(const unsigned* live, int u) {
+    return (live[u >> 5] >> (u & 31)) & 1u;
+}
+
+// Phase 1a: local ids and induced degrees (total and higher-priority part).
+// Rows up to kCoreWarpDeg: one warp each; longer rows: one block each.
+template <class V>
+__global__ void d1_core_map(const Problem<V>* __restrict__ Pp) {
     const Problem<V>& P = *Pp;
     State* st = P.st;
     if (*(volatile int*)&st->done || !*(volatile int*)&st->tail) return;
-    for (;;) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->push_cnt = 0;
-        assign_phase(P);
-        if (!grid_barrier(st)) break;
-        detect_phase(P, smem);
-        if (!grid_barrier(st)) break;
-        __shared__ int s_done;
-        if (blockIdx.x == 0 && threadIdx.x == 0) round_decide(P);
-        push_phase(P);
-        if (!grid_barrier(st)) break;
-        if (threadIdx.x == 0) s_done = *(volatile int*)&st->done;
+    const int cp = st->round & 1, np = cp ^ 1;
+    const int nS = st->ns[cp], nM = st->nm[cp], nL = st->nl[cp], k = nS + nM + nL;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->core_k = k;
+        st->core_par = np;
+    }
+    const CoreArrays A = core_arrays(P, np, k);
+    const unsigned long long seed = P.seed;
+    const bool use_deg = P.use_deg != 0;
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    for (int i = gw; i < k; i += nw) {
+        const int4 e = core_entry(P, cp, nS, nM, i);
+        const int v = e.x, d = e.z;
+        if (lane == 0) {
+            A.vid[i] = v;
+            A.lent[i] = e;
+            A.lcol[i] = P.col[v];
+            P.hlen[v] = i;
+        }
+        if (d > kCoreWarpDeg) continue;
+        const int g = P.g.graph(v), base = P.g.base(g);
+        const long long beg = P.g.begin(g, e.w);
+        const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
+        int cnt = 0, hcnt = 0;
+        for (int b0 = 0; b0 < d; b0 += 32) {
+            const int j = b0 + lane;
+            if (j < d) {
+                const int u = P.g.nbr(beg + j, base);
+                if (u != v && is_live(P.live, u)) {
+                    ++cnt;
+                    hcnt += higher(__ldg(P.deg + u), u, d, hv, v, base, seed, use_deg);
+                }
+            }
+        }
+        cnt = warp_sum(cnt);
+        hcnt = warp_sum(hcnt);
+        if (lane == 0) {
+            A.loff[i + 1] = cnt;
+            A.lhn[i] = hcnt;
+        }
+    }
+    __shared__ int s_cnt, s_hcnt;
+    for (int i = blockIdx.x; i < k; i += gridDim.x) {
+        const int4 e = core_entry(P, cp, nS, nM, i);
+        const int v = e.x, d = e.z;
+        if (d <= kCoreWarpDeg) continue;   // block-uniform
+        const int g = P.g.graph(v), base = P.g.base(g);
+        const long long beg = P.g.begin(g, e.w);
+        const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
+        if (threadIdx.x == 0) s_cnt = s_hcnt = 0;
         __syncthreads();
-        if (s_done) break;
+        int cnt = 0, hcnt = 0;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            const int u = P.g.nbr(beg + j, base);
+            if (u != v && is_live(P.live, u)) {
+                ++cnt;
+                hcnt += higher(__ldg(P.deg + u), u, d, hv, v, base, seed, use_deg);
+            }
+        }
+        cnt = warp_sum(cnt);
+        hcnt = warp_sum(hcnt);
+        if (lane == 0) {
+            atomicAdd(&s_cnt, cnt);
+            atomicAdd(&s_hcnt, hcnt);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A.loff[i + 1] = s_cnt;
+            A.lhn[i] = s_hcnt;
+        }
+        __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&st->bar_timeout) {
-        st->status = ST_BARRIER;
-        st->done = 1;
+}
+
+// Phase 1b (one block): offsets = exclusive scan of the induced degrees;
+// the first local worklist holds every local vertex.
+template <class V>
+__global__ void d1_core_scan(const Problem<V>* __restrict__ Pp) {
+    const Problem<V>& P = *Pp;
+    State* st = P.st;
+    if (*(volatile int*)&st->done || !*(volatile int*)&st->tail) return;
+    const int k = st->core_k;
+    const CoreArrays A = core_arrays(P, st->core_par, k);
+    __shared__ int s_part[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int per = (k + T - 1) / T;
+    const int lo = min(k, t * per), hi = min(k, lo + per);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += A.loff[i + 1];
+    s_part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {   // inclusive scan of the per-thread sums
+        const int x = t >= o ? s_part[t - o] : 0;
+        __syncthreads();
+        s_part[t] += x;
+        __syncthreads();
     }
+    int run = s_part[t] - sum;
+    for (int i = lo; i < hi; ++i) {
+        run += A.loff[i + 1];
+        A.loff[i + 1] = run;
+    }
+    if (t == 0) A.loff[0] = 0;
+    for (int i = t; i < k; i += T) A.lw0[i] = i;
+    if (t == 0) {
+        st->core_cur = k;
+        st->core_nxt = 0;
+        st->core_win = 0;
+    }
+}
+
+// Phase 1c: the induced lists, as local ids: higher-priority neighbors at
+// [loff[i], loff[i] + lhn[i]), the others after them.
+template <class V>
+__global__ void d1_core_fill(const Problem<V>* __restrict__ Pp) {
+    const Problem<V>& P = *Pp;
+    State* st = P.st;
+    if (*(volatile int*)&st->done || !*(volatile int*)&st->tail) return;
+    const int k = st->core_k;
+    const CoreArrays A = core_arrays(P, st->core_par, k);
+    int* adj = P.hadj;
+    const unsigned long long seed = P.seed;
+    const bool use_deg = P.use_deg != 0;
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = gw; i < k; i += nw) {
+        const int4 e = A.lent[i];
+        const int v = e.x, d = e.z;
+        if (d > kCoreWarpDeg) continue;
+        const int g = P.g.graph(v), base = P.g.base(g);
+        const long long beg = P.g.begin(g, e.w);
+        const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
+        int* hi_out = adj + A.loff[i];
+        int* lo_out = hi_out + A.lhn[i];
+        int hp = 0, op = 0;
+        for (int b0 = 0; b0 < d; b0 += 32) {
+            const int j = b0 + lane;
+            int u = -1;
+            bool keep = false, hi = false;
+            if (j < d) {
+                u = P.g.nbr(beg + j, base);
+                keep = u != v && is_live(P.live, u);
+                hi = keep && higher(__ldg(P.deg + u), u, d, hv, v, base, seed, use_deg);
+            }
+            const unsigned bh = __ballot_sync(kFullMask, hi);
+            const unsigned bo = __ballot_sync(kFullMask, keep && !hi);
+            if (hi) hi_out[hp + __popc(bh & lt)] = P.hlen[u];
+            else if (keep) lo_out[op + __popc(bo & lt)] = P.hlen[u];
+            hp += __popc(bh);
+            op += __popc(bo);
+        }
+    }
+    __shared__ int s_hp, s_op;
+    for (int i = blockIdx.x; i < k; i += gridDim.x) {
+        const int4 e = A.lent[i];
+        const int v = e.x, d = e.z;
+        if (d <= kCoreWarpDeg) continue;   // block-uniform
+        const int g = P.g.graph(v), base = P.g.base(g);
+        const long long beg = P.g.begin(g, e.w);
+        const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
+        int* hi_out = adj + A.loff[i];
+        int* lo_out = hi_out + A.lhn[i];
+        if (threadIdx.x == 0) s_hp = s_op = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < d; b0 += blockDim.x) {
+            const int j = b0 + threadIdx.x;
+            int u = -1;
+            bool keep = false, hi = false;
+            if (j < d) {
+                u = P.g.nbr(beg + j, base);
+                keep = u != v && is_live(P.live, u);
+                hi = keep && higher(__ldg(P.deg + u), u, d, hv, v, base, seed, use_deg);
+            }
+            const unsigned bh = __ballot_sync(kFullMask, hi);
+            const unsigned bo = __ballot_sync(kFullMask, keep && !hi);
+            int ph = 0, po = 0;
+            if (lane == 0) {
+                if (bh) ph = atomicAdd(&s_hp, __popc(bh));
+                if (bo) po = atomicAdd(&s_op, __popc(bo));
+            }
+            ph = __shfl_sync(kFullMask, ph, 0);
+            po = __shfl_sync(kFullMask, po, 0);
+            if (hi) hi_out[ph + __popc(bh & lt)] = P.hlen[u];
+            else if (keep) lo_out[po + __popc(bo & lt)] = P.hlen[u];
+        }
+        __syncthreads();
+    }
+}
+
+// End of a core round: trace, termination, next round's counts (one thread).
+template <class V>
+__device__ void core_decide(const Problem<V>& P) {
+    State* st = P.st;
+    const int r = st->round;
+    const long long cur = st->core_cur;
+    const long long nxt = *(volatile int*)&st->core_nxt;
+    if (r < P.trace_cap) {
+        P.trace_w[r] = nxt;
+        P.trace_s[r] = (long long)*(volatile unsigned long long*)&st->s_next;
+        P.trace_h[r] = (long long)*(volatile unsigned long long*)&st->h_next;
+    }
+    int done = 0, status = ST_OK;
+    if (nxt == 0) {
+        done = 1;
+    } else if (nxt >= cur) {
+        done = 1;
+        status = ST_NO_PROGRESS;
+    } else if (r >= P.max_rounds) {
+        done = 1;
+        status = ST_MAX_ROUNDS;
+    } else if (global_ns() - st->t0 > P.timeout_ns) {
+        done = 1;
+        status = ST_TIMEOUT;
+    }
+    if (!done) {
+        st->round = r + 1;
+        st->core_cur = (int)nxt;
+        st->core_nxt = 0;
+        st->s_next = 0ull;
+        st->h_next = 0ull;
+    }
+    st->status = status;
+    st->done = done;
+    __threadfence();
+}
+
+// Phase 2 (cooperative, kCoreBlocks x 1024 threads): the rounds.
+template <class V>
+__global__ void __launch_bounds__(1024, 1) d1_core_loop(const Problem<V>* __restrict__ Pp) {
+    const Problem<V>& P = *Pp;
+    State* st = P.st;
+    if (*(volatile int*)&st->done || !*(volatile int*)&st->tail) return;
+    const int k = st->core_k;
+    const CoreArrays A = core_arrays(P, st->core_par, k);
+    const int* adj = P.hadj;
+    int* lcol = A.lcol;
+    const bool batch = P.g_rounds != nullptr;
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    int side = 0;
+    for (;;) {
+        const int r = *(volatile int*)&st->round;
+        const int cur = *(volatile int*)&st->core_cur;
+        const int* lw = side ? A.lw1 : A.lw0;
+        int* lwn = side ? A.lw0 : A.lw1;
+        if (gt == 0) st->core_win = 0;   // read last in the previous round's push
+        // assign: first fit from the forbidden sets, from the previous color
+        for (int x = gt; x < cur; x += nt) {
+            const int i = lw[x];
+            lcol[i] = -first_fit(P, A.lent[i], -lcol[i]);
+        }
+        if (!grid_barrier(st)) break;
+        // detect: one warp per vertex over its higher-priority induced list
+        int my_max = 0;
+        unsigned long long my_s = 0ull, my_h = 0ull;
+        for (int x = gw; x < cur; x += nw) {
+            const int i = lw[x];
+            const int t = -lcol[i];
+            const int* h = adj + A.loff[i];
+            const int hn = A.lhn[i];
+            bool lose = false;
+            for (int b0 = 0; b0 < hn && !lose; b0 += 128) {
+                int c[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = b0 + 32 * j + lane;
+                    c[j] = e < hn ? lcol[h[e]] : 0;
+                }
+                bool hit = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) hit |= abs(c[j]) == t;
+                lose = __any_sync(kFullMask, hit);
+            }
+            if (lane == 0) {
+                const int4 e = A.lent[i];
+                const int g = batch ? P.g.graph(e.x) : 0;
+                if (lose) {
+                    lwn[atomicAdd(&st->core_nxt, 1)] = i;
+                    my_s += (unsigned long long)e.z;
+                    my_h += (unsigned long long)e.y;
+                    if (batch) atomicMax(P.g_rounds + g, r + 1);
+                } else {
+                    lcol[i] = t;
+                    A.qwin[atomicAdd(&st->core_win, 1)] = i;
+                    my_max = max(my_max, t);
+                    if (batch) atomicMax(P.g_colors + g, t);
+                }
+            }
+        }
+        my_max = warp_max(my_max);
+        my_s = warp_sum(my_s);
+        my_h = warp_sum(my_h);
+        if (lane == 0) {
+            if (my_max > 0) atomicMax(&st->max_color, my_max);
+            if (my_s > 0) atomicAdd(&st->s_next, my_s);
+            if (my_h > 0) atomicAdd(&st->h_next, my_h);
+        }
+        if (!grid_barrier(st)) break;
+        // push the winners' colors to their uncolored induced neighbors,
+        // while one thread closes the round.  The warps share the winners
+        // (several warps per winner when winners are few); a warp takes four
+        // list entries per lane at a time, and a neighbor's row start and
+        // degree come from its local entry, not from row_ptr.
+        if (gt == 0) core_decide(P);
+        const int nwin = *(volatile int*)&st->core_win;
+        if (nwin > 0) {
+            const int wpw = max(1, nw / nwin);   // warps per winner
+            const int slots = nw / wpw;
+            const int sub = gw % wpw;
+            for (int q = gw / wpw; q < nwin && gw < slots * wpw; q += slots) {
+                const int i = A.qwin[q];
+                const int c = lcol[i];
+                const int g = batch ? P.g.graph(A.vid[i]) : 0;
+                const int e1 = A.loff[i + 1];
+                const int step = wpw * 32;
+                for (int e0 = A.loff[i] + sub * 32 + lane; e0 < e1; e0 += 4 * step) {
+                    int j[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * step;
+                        j[u] = e < e1 ? adj[e] : -1;
+                    }
+                    int cj[4];
+                    int4 ej[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        cj[u] = j[u] >= 0 ? lcol[j[u]] : 1;
+                        ej[u] = j[u] >= 0 ? A.lent[j[u]] : make_int4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (cj[u] >= 0) continue;   // colored (or no entry)
+                        const int v = ej[u].x;
+                        if (c <= 64) {
+                            atomicOr(P.bm0 + v, 1ull << (c - 1));
+                        } else if (c - 1 <= ej[u].z) {
+                            const int b = c - 65;
+                            const long long bu = P.g.begin(g, ej[u].w);
+                            atomicOr(P.bmx + bm_offset(bu, v) + (b >> 5), 1u << (b & 31));
+                        }
+                    }
+                }
+            }
+        }
+        if (!grid_barrier(st)) break;
+        if (*(volatile int*)&st->done) break;
+        side ^= 1;
+    }
+    if (*(volatile int*)&st->bar_timeout) {
+        if (gt == 0) {
+            st->status = ST_BARRIER;
+            st->done = 1;
+        }
+        return;
+    }
+    // write the colors back
+    for (int i = gt; i < k; i += nt) P.col[A.vid[i]] = lcol[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -971,7 +1377,7 @@ struct Engine {
     struct Geometry {
         int grid, block;
         size_t smem;   // two warp appenders per warp
-        int tail_grid; // co-resident blocks for the cooperative tail kernel
+        int core_grid; // co-resident 1024-thread blocks of the cooperative core loop
         int det_grid;  // detect: its own occupancy
     };
 
@@ -980,7 +1386,7 @@ struct Engine {
         g->smem = (size_t)(o.block / 32) * 128 * sizeof(int4);
         if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
             for (const void* f : {(const void*)d1_classify<V>, (const void*)d1_tier<V>,
-                                  (const void*)d1_detect<V>, (const void*)d1_tail<V>})
+                                  (const void*)d1_detect<V>})
                 PGC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)g->smem));
         }
@@ -995,10 +1401,8 @@ struct Engine {
         }
         g->grid = dev.num_sms * per_sm;
         int t = 0;
-        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t, d1_tail<V>, o.block, g->smem));
-        // the tail's rounds are short and its phases meet at grid barriers:
-        // two blocks per SM keep those barriers cheap
-        g->tail_grid = dev.num_sms * std::max(1, std::min({t, std::max(per_sm, 1), 2}));
+        PGC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t, d1_core_loop<V>, 1024, 0));
+        g->core_grid = std::max(1, std::min(kCoreBlocks, dev.num_sms * std::max(t, 1)));
         return PGC_OK;
     }
 
@@ -1052,14 +1456,24 @@ struct Engine {
         PGC_CUDA(cudaGraphAddKernelNode(&b_asg, body, nullptr, 0, &k_asg));
         PGC_CUDA(cudaGraphAddKernelNode(&b_det, body, &b_asg, 1, &k_det));
         PGC_CUDA(cudaGraphAddKernelNode(&b_push, body, &b_det, 1, &k_push));
-        // the remaining small rounds: one cooperative launch
-        cudaKernelNodeParams k_tail = knode((void*)d1_tail<V>, g, g.smem, p_args);
-        k_tail.gridDim = dim3(g.tail_grid);
-        cudaGraphNode_t n_tail;
-        PGC_CUDA(cudaGraphAddKernelNode(&n_tail, graph, &n_loop, 1, &k_tail));
+        // the remaining small rounds: the core phase (no-ops unless the loop
+        // stopped with st->tail set)
+        cudaKernelNodeParams k_cmap = knode((void*)d1_core_map<V>, g, 0, p_args);
+        cudaKernelNodeParams k_cscan = knode((void*)d1_core_scan<V>, g, 0, p_args);
+        k_cscan.gridDim = dim3(1);
+        k_cscan.blockDim = dim3(1024);
+        cudaKernelNodeParams k_cfill = knode((void*)d1_core_fill<V>, g, 0, p_args);
+        cudaKernelNodeParams k_cloop = knode((void*)d1_core_loop<V>, g, 0, p_args);
+        k_cloop.gridDim = dim3(g.core_grid);
+        k_cloop.blockDim = dim3(1024);
+        cudaGraphNode_t n_cmap, n_cscan, n_cfill, n_cloop;
+        PGC_CUDA(cudaGraphAddKernelNode(&n_cmap, graph, &n_loop, 1, &k_cmap));
+        PGC_CUDA(cudaGraphAddKernelNode(&n_cscan, graph, &n_cmap, 1, &k_cscan));
+        PGC_CUDA(cudaGraphAddKernelNode(&n_cfill, graph, &n_cscan, 1, &k_cfill));
+        PGC_CUDA(cudaGraphAddKernelNode(&n_cloop, graph, &n_cfill, 1, &k_cloop));
         cudaLaunchAttributeValue coop = {};
         coop.cooperative = 1;
-        PGC_CUDA(cudaGraphKernelNodeSetAttribute(n_tail, cudaLaunchAttributeCooperative, &coop));
+        PGC_CUDA(cudaGraphKernelNodeSetAttribute(n_cloop, cudaLaunchAttributeCooperative, &coop));
         PGC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         g_grid = g.grid;
         g_det = g.det_grid;
@@ -1198,11 +1612,15 @@ struct Engine {
                                          stream));
                 PGC_CUDA(cudaStreamSynchronize(stream));
                 if (hs->done) break;
-                if (hs->tail) {   // the remaining rounds in one cooperative launch
-                    if (pgc_status s_ = kt.begin(6, "d1_tail")) return s_;
+                if (hs->tail) {   // the remaining rounds: the core phase
+                    if (pgc_status s_ = kt.begin(6, "d1_core")) return s_;
+                    d1_core_map<V><<<g.grid, g.block, 0, stream>>>(dP);
+                    d1_core_scan<V><<<1, 1024, 0, stream>>>(dP);
+                    d1_core_fill<V><<<g.grid, g.block, 0, stream>>>(dP);
+                    PGC_CUDA(cudaGetLastError());
                     void* args[] = {&dP};
-                    PGC_CUDA(cudaLaunchCooperativeKernel((void*)d1_tail<V>, dim3(g.tail_grid),
-                                                         dim3(g.block), args, g.smem, stream));
+                    PGC_CUDA(cudaLaunchCooperativeKernel((void*)d1_core_loop<V>, dim3(g.core_grid),
+                                                         dim3(1024), args, 0, stream));
                     if (pgc_status s_ = kt.end()) return s_;
                     break;
                 }
