@@ -598,6 +598,9 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     int my_max = 0;
     unsigned long long my_s = 0ull, my_h = 0ull;
     TierAppend app = tier_appender(smem);
+    // Round 1: every vertex holds tentative color 1, so v loses exactly when
+    // H(v) is not empty -- no list needs to be read.
+    const bool first = r == 1;
 
     // --- L tier: one block per vertex (static assignment) ---
     for (int i = blockIdx.x; i < nL; i += gridDim.x) {
@@ -606,9 +609,9 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
         const int g = P.g.graph(v);
         const long long beg = P.g.begin(g, ent.w);
         const int t = -col[v];
-        bool lose = false;
-        int nxt = (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
-        for (int b0 = 0; b0 < hl; b0 += blockDim.x) {
+        bool lose = first && hl > 0;
+        int nxt = !first && (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
+        for (int b0 = 0; !first && b0 < hl; b0 += blockDim.x) {
             const int u = nxt;
             const int e = b0 + blockDim.x + threadIdx.x;
             nxt = e < hl ? __ldg(ha + beg + e) : -1;
@@ -645,22 +648,22 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
         g = P.g.graph(ent.x);
         beg = P.g.begin(g, ent.w);
         t = -col[ent.x];
-        u0 = lane < ent.y ? __ldg(ha + beg + lane) : -1;
+        u0 = !first && lane < ent.y ? __ldg(ha + beg + lane) : -1;
     }
     for (int i = gw; i < nM; i += nw) {
         const int v = ent.x, hl = ent.y, d = ent.z;
         const int in = i + nw;
         int4 en = make_int4(-1, 0, 0, 0);
         if (in < nM) en = P.wm[cp][in];
-        bool lose = __any_sync(kFullMask, u0 >= 0 && abs(col[u0]) == t);
-        if (!lose && hl > 32) lose = warp_conflict(P, beg, hl, t, 32);
+        bool lose = first ? hl > 0 : __any_sync(kFullMask, u0 >= 0 && abs(col[u0]) == t);
+        if (!first && !lose && hl > 32) lose = warp_conflict(P, beg, hl, t, 32);
         int gn = 0, tn = 0, un = -1;
         long long bn = 0;
         if (in < nM) {
             gn = P.g.graph(en.x);
             bn = P.g.begin(gn, en.w);
             tn = -col[en.x];
-            un = lane < en.y ? __ldg(ha + bn + lane) : -1;
+            un = !first && lane < en.y ? __ldg(ha + bn + lane) : -1;
         }
         if (lane == 0) {
             if (lose) {
@@ -696,9 +699,10 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             const int v = ent.x, hl = ent.y, d = ent.z;
             g = P.g.graph(v);
             const long long beg = P.g.begin(g, ent.w);
-            int nxt = hl > 0 ? __ldg(ha + beg) : -1;
             t = -col[v];
-            for (int e = 0; e < hl; ++e) {
+            lose = first && hl > 0;
+            int nxt = !first && hl > 0 ? __ldg(ha + beg) : -1;
+            for (int e = 0; !first && e < hl; ++e) {
                 const int u = nxt;
                 nxt = e + 1 < hl ? __ldg(ha + beg + e + 1) : -1;
                 if (abs(col[u]) == t) {
