@@ -701,14 +701,12 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             const long long beg = P.g.begin(g, ent.w);
             t = -col[v];
             lose = first && hl > 0;
-            int nxt = !first && hl > 0 ? __ldg(ha + beg) : -1;
-            for (int e = 0; !first && e < hl; ++e) {
-                const int u = nxt;
-                nxt = e + 1 < hl ? __ldg(ha + beg + e + 1) : -1;
-                if (abs(col[u]) == t) {
-                    lose = true;
-                    break;
-                }
+            for (int e = 0; !first && e < hl && !lose; e += 4) {
+                int u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) lose |= u[j] >= 0 && abs(col[u[j]]) == t;
             }
             if (lose) {
                 my_s += (unsigned long long)d;
