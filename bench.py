@@ -474,7 +474,7 @@ def main():
                          "inside conditional graphs)")
     ap.add_argument("--tail-vertices", type=int, default=0,
                     help="worklist size below which the remaining rounds run in one "
-                         "cooperative launch (0: library default, < 0: never)")
+                         "cooperative launch on the subgraph the worklist induces (0: library default, < 0: never)")
     ap.add_argument("--timeout-ms", type=int, default=0,
                     help="device round-loop budget (raise it for runs under a profiler)")
     ap.add_argument("--no-batch", action="store_true")

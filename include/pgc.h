@@ -116,7 +116,8 @@ typedef struct {
     int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
     int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */
     int32_t tail_vertices;     /* D1: once the worklist has at most this many
-                                  vertices, the remaining rounds run in one
+                                  vertices, the remaining rounds run on the
+                                  subgraph the worklist induces, in one
                                   cooperative launch with grid barriers;
                                   0 => 4096, < 0 => never */
     pgc_profile *profile;      /* nullable */

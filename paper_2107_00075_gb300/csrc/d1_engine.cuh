@@ -1664,7 +1664,7 @@ struct Engine {
             case ST_MAX_ROUNDS: return fail(PGC_ERR_NO_CONVERGE, "max_rounds reached");
             case ST_TIMEOUT: return fail(PGC_ERR_TIMEOUT, "device round loop exceeded timeout_ms");
             case ST_BARRIER:
-                return fail(PGC_ERR_TIMEOUT, "a grid barrier of the tail kernel timed out");
+                return fail(PGC_ERR_TIMEOUT, "a grid barrier of the core loop timed out");
             default: return fail(PGC_ERR_CUDA, "unexpected device status");
         }
     }

@@ -73,6 +73,19 @@ def test_batch_no_degree_rule_and_geometry(pgc):
     check_against_oracle(b, colors, gr, gc, seed=5, recolor_degrees=False)
 
 
+@pytest.mark.parametrize("tail", [-1, 1 << 30])
+def test_batch_core_phase_hand_over(pgc, tail):
+    """The last rounds on the subgraph the worklist induces, with per-graph
+    ids, keys and statistics: from round 2 on (a threshold above every
+    worklist) or never."""
+    b = gen.make_batch(mixed_graphs(4))
+    colors, gr, gc, rounds = run_batch(pgc, b, seed=9, tail_vertices=tail)
+    check_against_oracle(b, colors, gr, gc, seed=9)
+    assert rounds == gr.max()
+    colors2, _, _, _ = run_batch(pgc, b, seed=9, tail_vertices=tail, flags=pgc.PGC_HOST_LOOP)
+    assert np.array_equal(colors, colors2)
+
+
 def test_batch_composition_does_not_change_results(pgc):
     gs = mixed_graphs(3)
     b1 = gen.make_batch(gs)

@@ -175,8 +175,8 @@ def test_repeatable_and_stream(pgc):
 
 @pytest.mark.parametrize("tail", [-1, 1, 100, 5000, 1 << 30])
 def test_tail_kernel_threshold_does_not_change_colors(pgc, tail):
-    """The last rounds run in one cooperative launch once the worklist is
-    small; where the hand-over happens must not change anything."""
+    """The last rounds run on the subgraph the worklist induces once the
+    worklist is small; where the hand-over happens must not change anything."""
     g = gen.rmat(14, 16, seed=11)
     assert_parity(pgc, g, seed=3, tail_vertices=tail)
     assert_parity(pgc, g, seed=3, tail_vertices=tail, flags=pgc.PGC_HOST_LOOP)
