@@ -239,7 +239,8 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
     State* st = P.st;
     const int warp = threadIdx.x >> 5;
     int4* sm4 = reinterpret_cast<int4*>(smem);
-    WarpAppend4 as = {sm4 + warp * 128, 0}, am = {sm4 + warp * 128 + 64, 0};
+    WarpAppend4 as = {sm4 + warp * 2 * kAppend4Slots, 0},
+                am = {sm4 + warp * 2 * kAppend4Slots + kAppend4Slots, 0};
     const int n = P.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n;
@@ -382,7 +383,8 @@ struct TierAppend {
 __device__ __forceinline__ TierAppend tier_appender(int* smem) {
     int4* sm4 = reinterpret_cast<int4*>(smem);
     const int warp = threadIdx.x >> 5;
-    return TierAppend{{sm4 + warp * 128, 0}, {sm4 + warp * 128 + 64, 0}};
+    return TierAppend{{sm4 + warp * 2 * kAppend4Slots, 0},
+                      {sm4 + warp * 2 * kAppend4Slots + kAppend4Slots, 0}};
 }
 
 // e = {v, |H(v)|, deg(v), local row start}
@@ -597,7 +599,9 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
     int my_max = 0;
     unsigned long long my_s = 0ull, my_h = 0ull;
-    TierAppend app = tier_appender(smem);
+    // losers keep their entry and tier: appended by source index
+    IdxAppend app_s = {smem + warp * 2 * kIdxSlots, 0};
+    IdxAppend app_m = {smem + warp * 2 * kIdxSlots + kIdxSlots, 0};
     // Round 1: every vertex holds tentative color 1, so v loses exactly when
     // H(v) is not empty -- no list needs to be read.
     const bool first = r == 1;
@@ -678,7 +682,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 queue_push(P, v, d);
             }
         }
-        tier_push(P, app, lose && lane == 0, ent, np);
+        ia_push(app_m, lose && lane == 0, i, P.wm[cp], P.wm[np], &st->nm[np]);
         ent = en;
         beg = bn;
         g = gn;
@@ -741,10 +745,10 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             graph_max(P.g_rounds, lose, g, r + 1);
             graph_max(P.g_colors, win, g, t);
         }
-        tier_push(P, app, lose, ent, np);
+        ia_push(app_s, lose, (int)i, P.ws[cp], P.ws[np], &st->ns[np]);
     }
-    wa4_flush(app.s, P.ws[np], &st->ns[np]);
-    wa4_flush(app.m, P.wm[np], &st->nm[np]);
+    ia_flush(app_s, P.ws[cp], P.ws[np], &st->ns[np]);
+    ia_flush(app_m, P.wm[cp], P.wm[np], &st->nm[np]);
 
     // --- per-warp totals ---
     my_max = warp_max(my_max);
@@ -1385,7 +1389,7 @@ struct Engine {
 
     pgc_status geometry(const Opts& o, Geometry* g) {
         g->block = o.block;
-        g->smem = (size_t)(o.block / 32) * 128 * sizeof(int4);
+        g->smem = (size_t)(o.block / 32) * 2 * kAppend4Slots * sizeof(int4);
         if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
             for (const void* f : {(const void*)d1_classify<V>, (const void*)d1_tier<V>,
                                   (const void*)d1_detect<V>})

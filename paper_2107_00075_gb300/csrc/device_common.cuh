@@ -45,12 +45,16 @@ namespace pgc {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // Warp-aggregated worklist append: lanes push (pred, v); a per-warp shared
-// buffer of 64 slots is flushed 32 entries at a time with one atomicAdd, so
-// list writes are coalesced and counter atomics are 32x fewer.  All 32
-// lanes must call wa_push / wa_flush together.
+// buffer of kAppendSlots entries is flushed kAppendFlush entries at a time
+// with one atomicAdd, so list writes are coalesced and the list counter --
+// one address that every warp of the grid hits -- takes kAppendFlush times
+// fewer atomics.  All 32 lanes must call wa_push / wa_flush together.
+constexpr int kAppendFlush = 96;                // a multiple of 32
+constexpr int kAppendSlots = kAppendFlush + 32; // per appender
+
 struct WarpAppend {
-    int* buf;    // 64 ints of shared memory owned by this warp
-    int count;   // warp-uniform, < 32 between calls
+    int* buf;    // kAppendSlots ints of shared memory owned by this warp
+    int count;   // warp-uniform, < kAppendFlush between calls
 };
 
 __device__ __forceinline__ void wa_push(WarpAppend& a, bool pred, int v, int* out, int* out_cnt) {
@@ -59,13 +63,14 @@ __device__ __forceinline__ void wa_push(WarpAppend& a, bool pred, int v, int* ou
     if (pred) a.buf[a.count + __popc(m & ((1u << lane) - 1u))] = v;
     a.count += __popc(m);
     __syncwarp();
-    if (a.count >= 32) {
+    if (a.count >= kAppendFlush) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(out_cnt, 32);
+        if (lane == 0) base = atomicAdd(out_cnt, kAppendFlush);
         base = __shfl_sync(kFullMask, base, 0);
-        out[base + lane] = a.buf[lane];
-        const int rem = a.count - 32;
-        const int tmp = (int)lane < rem ? a.buf[32 + lane] : 0;
+#pragma unroll
+        for (int k = 0; k < kAppendFlush; k += 32) out[base + k + lane] = a.buf[k + lane];
+        const int rem = a.count - kAppendFlush;
+        const int tmp = (int)lane < rem ? a.buf[kAppendFlush + lane] : 0;
         __syncwarp();
         if ((int)lane < rem) a.buf[lane] = tmp;
         a.count = rem;
@@ -79,7 +84,7 @@ __device__ __forceinline__ void wa_flush(WarpAppend& a, int* out, int* out_cnt) 
     int base = 0;
     if (lane == 0) base = atomicAdd(out_cnt, a.count);
     base = __shfl_sync(kFullMask, base, 0);
-    if ((int)lane < a.count) out[base + lane] = a.buf[lane];
+    for (int k = lane; k < a.count; k += 32) out[base + k] = a.buf[k];
     a.count = 0;
     __syncwarp();
 }
@@ -106,7 +111,14 @@ __device__ __forceinline__ long long bitmap_offset(int rp_v, int v) {
 
 namespace pgc {
 
-// WarpAppend for 16-byte entries (a 64-entry int4 buffer per warp).
+// WarpAppend for 16-byte entries (kAppend4Slots int4 per appender).  Its
+// buffer is kept at 32 + 32 entries: the distance-1 detection kernel that
+// uses it relies on L1, and a larger shared buffer costs more L1 than the
+// saved counter atomics are worth (measured: round 2 of R-MAT-24 took 50%
+// longer with 96-entry flushes).
+constexpr int kAppend4Flush = 32;
+constexpr int kAppend4Slots = kAppend4Flush + 32;
+
 struct WarpAppend4 {
     int4* buf;
     int count;
@@ -119,19 +131,66 @@ __device__ __forceinline__ void wa4_push(WarpAppend4& a, bool pred, int4 e, int4
     if (pred) a.buf[a.count + __popc(m & ((1u << lane) - 1u))] = e;
     a.count += __popc(m);
     __syncwarp();
-    if (a.count >= 32) {
+    if (a.count >= kAppend4Flush) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(out_cnt, 32);
+        if (lane == 0) base = atomicAdd(out_cnt, kAppend4Flush);
         base = __shfl_sync(kFullMask, base, 0);
-        out[base + lane] = a.buf[lane];
-        const int rem = a.count - 32;
+#pragma unroll
+        for (int k = 0; k < kAppend4Flush; k += 32) out[base + k + lane] = a.buf[k + lane];
+        const int rem = a.count - kAppend4Flush;
         int4 tmp = make_int4(0, 0, 0, 0);
-        if ((int)lane < rem) tmp = a.buf[32 + lane];
+        if ((int)lane < rem) tmp = a.buf[kAppend4Flush + lane];
         __syncwarp();
         if ((int)lane < rem) a.buf[lane] = tmp;
         a.count = rem;
         __syncwarp();
     }
+}
+
+// Re-append of entries that already sit in a source list (a loser keeps
+// its entry for the next round): the shared buffer holds 4-byte source
+// indices instead of 16-byte entries, so the same shared memory takes
+// kIdxFlush entries per counter atomic; the flush copies the entries from
+// the source list (just read, so mostly cache hits).
+constexpr int kIdxFlush = 224;
+constexpr int kIdxSlots = kIdxFlush + 32;
+
+struct IdxAppend {
+    int* buf;    // kIdxSlots ints of shared memory owned by this warp
+    int count;   // warp-uniform, < kIdxFlush between calls
+};
+
+__device__ __forceinline__ void ia_push(IdxAppend& a, bool pred, int idx, const int4* src,
+                                        int4* out, int* out_cnt) {
+    const unsigned lane = lane_id();
+    const unsigned m = __ballot_sync(kFullMask, pred);
+    if (pred) a.buf[a.count + __popc(m & ((1u << lane) - 1u))] = idx;
+    a.count += __popc(m);
+    __syncwarp();
+    if (a.count >= kIdxFlush) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(out_cnt, kIdxFlush);
+        base = __shfl_sync(kFullMask, base, 0);
+#pragma unroll
+        for (int k = 0; k < kIdxFlush; k += 32) out[base + k + lane] = src[a.buf[k + lane]];
+        const int rem = a.count - kIdxFlush;
+        const int tmp = (int)lane < rem ? a.buf[kIdxFlush + lane] : 0;
+        __syncwarp();
+        if ((int)lane < rem) a.buf[lane] = tmp;
+        a.count = rem;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void ia_flush(IdxAppend& a, const int4* src, int4* out, int* out_cnt) {
+    if (a.count == 0) return;
+    const unsigned lane = lane_id();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(out_cnt, a.count);
+    base = __shfl_sync(kFullMask, base, 0);
+    for (int k = lane; k < a.count; k += 32) out[base + k] = src[a.buf[k]];
+    a.count = 0;
+    __syncwarp();
 }
 
 __device__ __forceinline__ void wa4_flush(WarpAppend4& a, int4* out, int* out_cnt) {
@@ -140,7 +199,7 @@ __device__ __forceinline__ void wa4_flush(WarpAppend4& a, int4* out, int* out_cn
     int base = 0;
     if (lane == 0) base = atomicAdd(out_cnt, a.count);
     base = __shfl_sync(kFullMask, base, 0);
-    if ((int)lane < a.count) out[base + lane] = a.buf[lane];
+    for (int k = lane; k < a.count; k += 32) out[base + k] = a.buf[k];
     a.count = 0;
     __syncwarp();
 }

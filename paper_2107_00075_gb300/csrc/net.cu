@@ -65,7 +65,7 @@ struct Problem {
     const int* r_idx;
     int* col;
     unsigned long long* key;    // priority key (see net_init)
-    int* lose;
+    int* lose;                  // = the round in which the vertex lost (0: never)
     int* net_flag;              // = round number while the net is active
     unsigned long long* mask;   // [window][net]
     int* wt[2];
@@ -113,7 +113,8 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
     const Problem& P = *Pp;
     State* st = P.st;
     const int warp = threadIdx.x >> 5;
-    WarpAppend at = {smem + warp * 128, 0}, aw = {smem + warp * 128 + 64, 0};
+    WarpAppend at = {smem + warp * 2 * kAppendSlots, 0},
+               aw = {smem + warp * 2 * kAppendSlots + kAppendSlots, 0};
     int my_bound = 0;
     unsigned long long my_h = 0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -187,8 +188,17 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
         const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
         int t = 0;
         for (int w = 0; w < P.windows && t == 0; ++w) {
+            // four nets at a time: their ids, then their mask words
+            const unsigned long long* mw = mk + w * nn;
             unsigned long long f = 0ull;
-            for (int j = 0; j < k; ++j) f |= mk[w * nn + vertex_net(P, v, beg, j)];
+            for (int j = 0; j < k; j += 4) {
+                int q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) q[u] = j + u < k ? vertex_net(P, v, beg, j + u) : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q[u] >= 0) f |= mw[q[u]];
+            }
             if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
         }
         if (t == 0) {
@@ -279,7 +289,7 @@ __device__ __forceinline__ bool key_priority(unsigned long long ku, int u, unsig
     return u < v;
 }
 
-__device__ void big_net_detect(const Problem& P, int q, int m, int lane) {
+__device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) {
     const unsigned long long seed = P.seed;
     for (int i0 = 0; i0 < m; i0 += 32) {
         int x = -1, c = 0;
@@ -311,14 +321,15 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane) {
                 if (c && cs == c && ys != x && key_priority(ks, ys, kx, x, seed)) lose = true;
             }
         }
-        if (lose) P.lose[x] = 1;
+        if (lose) P.lose[x] = r;
     }
 }
 
 // Loads the colors and keys of up to kDetRows rows of members (x < 0: no
 // member) and flags the losers.  id: 1 + the net's index within its row.
 __device__ __forceinline__ void resolve_rows(const Problem& P, const int (&x)[kDetRows],
-                                             const int (&id)[kDetRows], unsigned long long seed) {
+                                             const int (&id)[kDetRows], unsigned long long seed,
+                                             int r) {
     int cx[kDetRows];
     unsigned long long kx[kDetRows];
 #pragma unroll
@@ -336,7 +347,7 @@ __device__ __forceinline__ void resolve_rows(const Problem& P, const int (&x)[kD
         const int c = cx[k] < 0 ? -cx[k] : 0;
         const unsigned tag = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
         const unsigned g = __match_any_sync(kFullMask, tag);
-        if (c && __popc(g) > 1 && group_loses(g, x[k], kx[k], seed)) P.lose[x[k]] = 1;
+        if (c && __popc(g) > 1 && group_loses(g, x[k], kx[k], seed)) P.lose[x[k]] = r;
     }
 }
 
@@ -386,7 +397,7 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
                                     : __ldg(P.m_idx + bg + lane);
                     }
                 }
-                resolve_rows(P, x, id, seed);
+                resolve_rows(P, x, id, seed, r);
             }
         } else if (sm) {
             // exclusive scan of the small nets' sizes = their packed starts
@@ -434,7 +445,7 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
                     }
                     r0 = r1;
                 }
-                resolve_rows(P, x, id, seed);
+                resolve_rows(P, x, id, seed, r);
             }
         }
         // nets of more than 32 members, one at a time
@@ -444,7 +455,7 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
             bg &= bg - 1;
             const int qb = __shfl_sync(kFullMask, q, src);
             const int mb = __shfl_sync(kFullMask, m, src);
-            big_net_detect(P, qb, mb, lane);
+            big_net_detect(P, qb, mb, lane, r);
         }
         __syncwarp();
     }
@@ -482,8 +493,11 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
         status = ST_TIMEOUT;
     }
     if (!done) {
-        // when the next worklist touches about every net, skip the marking
-        st->all_active = *(volatile unsigned long long*)&st->h_next >= 2ull * (unsigned long long)P.n_nets;
+        // when the next worklist touches about every net (its vertices' net
+        // memberships, estimated from the average, reach twice the nets),
+        // skip the marking
+        st->all_active = (unsigned long long)nxt * st->h_first >=
+                         2ull * (unsigned long long)P.n_nets * (unsigned long long)P.n;
         st->nt[cp] = st->nw[cp] = 0;
         st->round = r + 1;
         st->s_next = 0ull;
@@ -507,7 +521,8 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
     const long long total = (long long)nT + nW;
     const long long nn = P.n_nets;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    WarpAppend at = {smem + warp * 128, 0}, aw = {smem + warp * 128 + 64, 0};
+    WarpAppend at = {smem + warp * 2 * kAppendSlots, 0},
+               aw = {smem + warp * 2 * kAppendSlots + kAppendSlots, 0};
     int my_max = 0;
     unsigned long long my_s = 0ull, my_h = 0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -519,15 +534,16 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
         if (i < total) {
             thread_tier = i < nT;
             v = thread_tier ? P.wt[cp][i] : P.ww[cp][i - nT];
-            const int beg = __ldg(P.r_ptr + v);
-            const int d = __ldg(P.r_ptr + v + 1) - beg;
-            const int k = d + P.self;
-            if (P.lose[v]) {
-                P.lose[v] = 0;
+            if (P.lose[v] == r) {   // lost this round: only the trace needs its degree
                 lost = true;
-                my_s += (unsigned long long)d;
-                my_h += (unsigned long long)k;
+                if (P.trace_cap > 0) {
+                    const int d = __ldg(P.r_ptr + v + 1) - __ldg(P.r_ptr + v);
+                    my_s += (unsigned long long)d;
+                    my_h += (unsigned long long)(d + P.self);
+                }
             } else {
+                const int beg = __ldg(P.r_ptr + v);
+                const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
                 const int t = -P.col[v];
                 P.col[v] = t;
                 my_max = max(my_max, t);
@@ -633,7 +649,7 @@ struct Geometry {
 
 static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
     g->block = o.block;
-    g->smem = (size_t)(o.block / 32) * 128 * sizeof(int);
+    g->smem = (size_t)(o.block / 32) * 2 * kAppendSlots * sizeof(int);
     g->det_smem = (size_t)(o.block / 32) * kDetSmemInts * sizeof(int);
     int per_sm = o.grid_per_sm;
     if (per_sm == 0) {

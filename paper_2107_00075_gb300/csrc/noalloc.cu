@@ -138,7 +138,7 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
 
     const int block = 256;
     const int grid = sms * 4;
-    const size_t smem = (size_t)(block / 32) * 128 * sizeof(int4);
+    const size_t smem = (size_t)(block / 32) * 2 * kAppend4Slots * sizeof(int4);
     const cudaGraphConditionalHandle none = 0;
     d1_classify<SingleView><<<grid, block, smem, stream>>>(dP);
     d1_build<SingleView><<<grid, block, 0, stream>>>(dP);
