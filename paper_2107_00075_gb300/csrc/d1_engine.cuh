@@ -572,12 +572,18 @@ template <class V>
 __device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg, int hl, int t,
                                               int from) {
     const int lane = lane_id();
-    int nxt = from + lane < hl ? __ldg(P.hadj + beg + from + lane) : -1;
-    for (int b0 = from; b0 < hl; b0 += 32) {
-        const int u = nxt;
-        const int e = b0 + 32 + lane;
-        nxt = e < hl ? __ldg(P.hadj + beg + e) : -1;
-        if (__any_sync(kFullMask, u >= 0 && abs(P.col[u]) == t)) return true;
+    const int* h = P.hadj + beg;
+    for (int b0 = from; b0 < hl; b0 += 32 * 2) {
+        int u[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int e = b0 + 32 * j + lane;
+            u[j] = e < hl ? __ldg(h + e) : -1;
+        }
+        bool hit = false;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) hit |= u[j] >= 0 && abs(P.col[u[j]]) == t;
+        if (__any_sync(kFullMask, hit)) return true;
     }
     return false;
 }
