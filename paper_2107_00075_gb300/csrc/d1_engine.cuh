@@ -363,10 +363,16 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
         const long long beg = P.g.begin(g, ent.w);
         const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
         int pos = 0;
-        for (int e = 0; e < d; ++e) {
-            const int u = P.g.nbr(beg + e, base);
-            if (u != v && higher(__ldg(dg + u), u, d, hv, v, base, seed, use_deg))
-                P.hadj[beg + pos++] = u;
+        for (int e0 = 0; e0 < d; e0 += 4) {
+            int u[4], du[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[j] = e0 + j < d ? P.g.nbr(beg + e0 + j, base) : v;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) du[j] = u[j] != v ? __ldg(dg + u[j]) : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (u[j] != v && higher(du[j], u[j], d, hv, v, base, seed, use_deg))
+                    P.hadj[beg + pos++] = u[j];
         }
         P.hlen[v] = pos;
         my_h += (unsigned long long)pos;
