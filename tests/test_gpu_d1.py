@@ -109,6 +109,22 @@ def test_host_arrays_are_staged(pgc):
     assert np.array_equal(r.colors, want.colors) and r.rounds == want.rounds
 
 
+def test_pinned_host_arrays(pgc):
+    """Pinned host arrays (what the end-to-end measurement passes): staged
+    on the device, colored, copied back; repeated calls on the same buffers,
+    with validation and with the host-driven loop, all equal the oracle."""
+    import torch
+    g = gen.rmat(14, 16, seed=6)
+    rp = torch.from_numpy(g.row_ptr).pin_memory()
+    ci = torch.from_numpy(g.col_idx).pin_memory()
+    out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    want = oracle.color_d1(g.row_ptr, g.col_idx, seed=8)
+    for flags in (0, 0, pgc.PGC_VALIDATE, pgc.PGC_HOST_LOOP):
+        r = pgc.pgc_color_d1(rp, ci, seed=8, colors=out, flags=flags)
+        assert np.array_equal(out.numpy(), want.colors), flags
+        assert r.rounds == want.rounds and r.num_colors == want.num_colors
+
+
 def test_edge_cases(pgc):
     import torch
     # n = 0
