@@ -108,10 +108,10 @@ typedef struct {
     uint32_t flags;            /* PGC_* flags above */
     int32_t max_rounds;        /* 0 => n + 1 (an upper bound: each round commits
                                   the worklist vertex with the largest key) */
-    int32_t mid_degree;        /* 0 => 32: a vertex whose per-round scan list
+    int32_t mid_degree;        /* 0 => 64: a vertex whose per-round scan list
                                   (D1: neighbors with higher priority) is longer
                                   gets a warp instead of a thread */
-    int32_t hub_degree;        /* 0 => 1024: longer lists get a thread block */
+    int32_t hub_degree;        /* 0 => 16384: longer lists get a thread block */
     int32_t block;             /* 0 => default threads per block (128..1024) */
     int32_t grid_per_sm;       /* 0 => occupancy-derived blocks per SM */
     int32_t timeout_ms;        /* 0 => 60000: device loop gives up after this */

@@ -47,8 +47,8 @@ bool is_host_pointer(const void* p);
 struct Opts {
     uint32_t flags = 0;
     int32_t max_rounds = 0;
-    int32_t mid_degree = 32;
-    int32_t hub_degree = 1024;
+    int32_t mid_degree = 64;
+    int32_t hub_degree = 16384;
     int32_t block = 256;
     int32_t grid_per_sm = 0;
     int32_t timeout_ms = 60000;
