@@ -31,17 +31,21 @@
 // |col[u]| is u's current color during detection; a winner flips its own
 // sign in place without disturbing concurrent readers.
 //
-// Work decomposition (no thread waits for another; no result depends on it):
-//   detect, by |H(v)|: up to 32 entries one thread per vertex; up to 1024
-//   one warp per vertex; longer lists one thread block per vertex.  Scans
-//   step through the list one entry per thread, loading the next step's ids
-//   while the current step's colors are gathered, and a loser stops at the
-//   step that finds its conflict.  Setup cuts long rows into 512-entry items
-//   and push into 128-entry items, one warp each (no decision depends on
-//   them).
+// Work decomposition (no result depends on it):
+//   detect, by |H(v)| (defaults; options mid_degree / hub_degree): up to 64
+//   entries one thread per vertex; up to 16384 one warp per vertex; longer
+//   lists one thread block per vertex.  A loser stops at the step that finds
+//   its conflict.  In round 1 every vertex holds color 1, so v loses exactly
+//   when H(v) is not empty and no list is read.  Losers keep their worklist
+//   entry: they are re-appended by source index (the list counters are the
+//   hottest atomics of the kernel).  Setup cuts long rows into 512-entry
+//   items and push into 128-entry items, one warp each.
 // The round loop runs on the device: a CUDA graph with a conditional WHILE
 // node around {assign, detect, push}; the last block of detect updates the
-// round state and sets the loop condition.
+// round state and sets the loop condition.  Once the worklist has at most
+// tail_w vertices the remaining rounds run in the core phase: on the
+// subgraph the worklist induces, in one cooperative launch whose blocks
+// meet at (bounded) grid barriers -- the only waits in the engine.
 //
 // Batches: graph g owns global vertices [vtx_off[g], vtx_off[g+1]); ids,
 // the priority hash and degrees are graph-local, so every graph is colored

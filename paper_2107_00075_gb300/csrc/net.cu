@@ -14,9 +14,11 @@
 // Per round:
 //   assign  v in W: forbidden(v) = OR of the color masks of v's nets;
 //           t = first free color (Alg. 1); col[v] = -t.  Marks v's nets
-//           active for this round.
-//   detect  one warp per active net: each uncolored member v whose color is
-//           also held by a member with priority loses (Alg. 5 + Alg. 4).
+//           active for this round (skipped while W's nets cover them all).
+//   detect  per active net: each uncolored member v whose color is also
+//           held by a member with priority loses (Alg. 5 + Alg. 4); small
+//           nets are packed into 32-lane rows and each (net, color) group
+//           keeps only its highest-priority member (warp reductions).
 //   commit  v in W: losers form W_{r+1}; a winner commits and sets bit t in
 //           the masks of its nets (so a mask is always the OR of its
 //           committed members' colors, kept incrementally: each vertex
