@@ -38,7 +38,7 @@ std::vector<std::function<void()>>& release_hooks();
 
 namespace net {
 
-constexpr int kThreadNets = 32;   // vertices with up to this many nets: one thread
+constexpr int kThreadNets = 64;   // vertices with up to this many nets: one thread
 constexpr int kMaxWindows = 64;   // masks hold colors 1..64*windows (<= 4096)
 
 enum : int { ST_OK = 0, ST_NO_PROGRESS = 1, ST_MAX_ROUNDS = 2, ST_TIMEOUT = 3, ST_OVERFLOW = 4 };
