@@ -253,8 +253,9 @@ static pgc_status color_batch(int32_t G, const int64_t* vtx_off, const int64_t* 
             }
         }
         if (!have) {
-            static const Tuned cand[] = {{128, 16, 256}, {256, 16, 256}, {256, 32, 1024},
-                                         {512, 32, 1024}, {256, 64, 4096}, {512, 64, 4096}};
+            static const Tuned cand[] = {{128, 16, 256},  {256, 16, 256},   {256, 32, 1024},
+                                         {512, 32, 1024}, {256, 64, 4096},  {512, 64, 4096},
+                                         {256, 64, 16384}, {256, 128, 16384}};
             cudaEvent_t a, b;
             PGC_CUDA(cudaEventCreate(&a));
             PGC_CUDA(cudaEventCreate(&b));
