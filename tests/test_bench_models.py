@@ -1,0 +1,64 @@
+"""CPU checks of what bench.py reports: the byte models behind the roofline
+(hand-computed on a small trace) and the JSON line of the reference arm."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_design_bytes_on_a_hand_trace():
+    # three rounds: |W| = 10, 6, 2; S = 40, 30, 8; H = 20, 12, 4; n = 10, nnz = 40
+    w, s, h = [10, 6, 2], [40, 30, 8], [20, 12, 4]
+    b = bench.d1_algorithmic_bytes(w, s, h, 10, 40)
+    assert b["d1_classify"] == 4 * 11 + 24 * 10
+    assert b["d1_build"] == 16 * 10 + 8 * 40 + 4 * 20
+    assert b["d1_tier"] == 8 * 10
+    assert b["d1_assign"] == 16 * 6 + 16 * 2          # no assign in round 1
+    assert b["d1_detect"] == 20 * (10 + 6 + 2) + 8 * (20 + 12 + 4)
+    # pushes: adjacency of each round's winners, S_r - S_{r+1}
+    assert b["d1_push"] == 12 * ((40 - 30) + (30 - 8) + 8)
+    assert "d1_core" not in b
+
+
+def test_design_bytes_split_at_the_core_phase():
+    w, s, h = [10, 6, 2], [40, 30, 8], [20, 12, 4]
+    whole = bench.d1_algorithmic_bytes(w, s, h, 10, 40)
+    split = bench.d1_algorithmic_bytes(w, s, h, 10, 40, tail_at=2)
+    assert split["d1_detect"] == 20 * (10 + 6) + 8 * (20 + 12)
+    total = lambda d: sum(d[k] for k in ("d1_assign", "d1_detect", "d1_push", "d1_core")
+                          if k in d)
+    assert total(split) == pytest.approx(total(whole))
+
+
+def test_method_bytes_on_a_hand_trace():
+    w, s = [10, 6, 2], [40, 30, 8]
+    tot, rounds = bench.d1_method_bytes(w, s, 10, 40)
+    r1 = 4 * 11 + 8 * 40 + 4 * 10 + 4 * 6
+    r2 = 16 * 6 + 8 * 30 + 4 * 2
+    r3 = 16 * 2 + 8 * 8 + 4 * 0
+    assert rounds == 3 and tot == r1 + r2 + r3
+    tot2, rounds2 = bench.d1_method_bytes(w, s, 10, 40, tail_at=1)
+    assert rounds2 == 1 and tot2 == r1
+
+
+def test_reference_arm_json_line():
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3", "--reference-scale", "10"],
+                       capture_output=True, text=True, cwd=ROOT, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["warmup"] >= 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+    assert np.isclose(line["e2e"]["value"], line["value"])
