@@ -54,6 +54,8 @@ static Staging& staging_for(int device) {
     return *p;
 }
 
+constexpr int kOverlapMinEntries = 1 << 24;   // smaller host adjacencies are copied whole
+
 static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, uint64_t seed,
                         int32_t* colors, int32_t* rounds, int32_t* num_colors,
                         const pgc_opts* opts, void* stream_v) {
@@ -80,6 +82,7 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
     const int* d_ci = col_idx;
     int* d_col = colors;
     int nnz = 0;
+    bool overlap = false;
     if (host_rp) {
         nnz = row_ptr[n];
     } else {
@@ -100,8 +103,14 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
         }
         if (host_ci && nnz > 0) {
             if (pgc_status s = stg.ci.ensure((size_t)nnz * 4)) return s;
-            PGC_CUDA(cudaMemcpyAsync(stg.ci.ptr, col_idx, (size_t)nnz * 4,
-                                     cudaMemcpyHostToDevice, stream));
+            // a large host adjacency is uploaded by the engine in row ranges
+            // that overlap the list build (device-side round loop only);
+            // otherwise it is copied before the coloring starts
+            overlap = host_rp && nnz >= kOverlapMinEntries &&
+                      !(o.flags & (PGC_VALIDATE | PGC_HOST_LOOP));
+            if (!overlap)
+                PGC_CUDA(cudaMemcpyAsync(stg.ci.ptr, col_idx, (size_t)nnz * 4,
+                                         cudaMemcpyHostToDevice, stream));
             d_ci = stg.ci.as<int>();
         }
     }
@@ -133,8 +142,9 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
         }
     }
     SingleView view{d_rp, d_ci};
+    const Upload up{col_idx, row_ptr, stg.ci.as<int>()};
     pgc_status s = cx->run(view, n, nnz, d_col, nullptr, nullptr, seed, o, stream, rounds,
-                           num_colors);
+                           num_colors, overlap ? &up : nullptr);
     if (s != PGC_OK) return s;
     if (host_col) {
         PGC_CUDA(cudaMemcpyAsync(colors, d_col, (size_t)n * 4, cudaMemcpyDeviceToHost, stream));

@@ -290,10 +290,12 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
 }
 
 // ---------------------------------------------------------------------------
-// setup 2: H(v) = neighbors with higher priority, stored at v's row start
+// setup 2: H(v) = neighbors with higher priority, stored at v's row start.
+// Only the vertices in [lo, hi) (one launch may cover a part of the graph,
+// so the rest of the adjacency can still be on its way to the device).
 // ---------------------------------------------------------------------------
 template <class V>
-__global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
+__global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp, int lo, int hi) {
     const Problem<V>& P = *Pp;
     State* st = P.st;
     const int* __restrict__ dg = P.deg;
@@ -308,6 +310,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
     for (int q = gw; q < nC; q += nw) {
         const int2 it = P.items[q];
         const int v = it.x;
+        if (v < lo || v >= hi) continue;
         const int g = P.g.graph(v), base = P.g.base(g);
         long long beg;
         int d;
@@ -336,6 +339,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
     for (int i = gw; i < nM; i += nw) {
         const int4 ent = P.wm[0][i];
         const int v = ent.x, d = ent.z;
+        if (v < lo || v >= hi) continue;
         const int g = P.g.graph(v), base = P.g.base(g);
         const long long beg = P.g.begin(g, ent.w);
         const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
@@ -363,6 +367,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += stride) {
         const int4 ent = P.ws[0][i];
         const int v = ent.x, d = ent.z;
+        if (v < lo || v >= hi) continue;
         const int g = P.g.graph(v), base = P.g.base(g);
         const long long beg = P.g.begin(g, ent.w);
         const uint64_t hv = prio_hash(seed, (uint32_t)(v - base));
@@ -896,7 +901,18 @@ __device__ __forceinline__ bool grid_barrier(State* st) {
 // scanned; the induced lists are a subset of W's adjacency, so they fit),
 // per-vertex arrays in the other parity's worklist buffers (3 x 16n bytes).
 
-constexpr int kCoreBlocks = 32;     // blocks of the core loop (1024 threads each)
+constexpr int kCoreBlocks = 32;
+constexpr int kUploadChunks = 4;    // host adjacency uploaded in this many row ranges
+
+// Adjacency still in (pinned) host memory when a coloring starts: it is
+// copied in kUploadChunks row ranges on a second stream, and the list build
+// of each range starts as soon as its rows have arrived, so the transfer
+// overlaps the build.
+struct Upload {
+    const int* h_ci;   // host adjacency
+    const int* h_rp;   // host row offsets (chunk boundaries)
+    int* d_ci;         // device copy (the view's adjacency)
+};     // blocks of the core loop (1024 threads each)
 constexpr int kCoreWarpDeg = 4096;  // rows up to this length: one warp; longer: one block
 
 struct CoreArrays {
@@ -1375,20 +1391,36 @@ struct Engine {
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     int last_want_trace = 0, last_tcap = 1;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle handle = 0;
+    // [0]: setup + rounds; [1]: rounds only (setup enqueued by the host
+    // while the adjacency is still being uploaded)
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int g_grid = 0, g_block = 0, g_det = 0;
+    cudaStream_t up_stream = nullptr;             // adjacency upload
+    cudaEvent_t up_fork = nullptr, up_done[kUploadChunks] = {};
 
     void destroy_graph() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
+        for (int k = 0; k < 2; ++k) {
+            if (exec[k]) cudaGraphExecDestroy(exec[k]);
+            if (graph[k]) cudaGraphDestroy(graph[k]);
+            exec[k] = nullptr;
+            graph[k] = nullptr;
+        }
         g_grid = 0;
+    }
+
+    void destroy_upload() {
+        if (up_stream) cudaStreamDestroy(up_stream);
+        if (up_fork) cudaEventDestroy(up_fork);
+        for (cudaEvent_t& e : up_done)
+            if (e) cudaEventDestroy(e);
+        up_stream = nullptr;
+        up_fork = nullptr;
+        for (cudaEvent_t& e : up_done) e = nullptr;
     }
     void release() {
         destroy_graph();
+        destroy_upload();
         for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &live, &ws, &wm, &wl, &items, &pushq,
                           &state, &problem, &trace})
             b->release();
@@ -1440,12 +1472,26 @@ struct Engine {
 
     pgc_status build_graph(const Geometry& g) {
         destroy_graph();
+        for (int k = 0; k < 2; ++k)
+            if (pgc_status s = build_one_graph(g, k == 0, &graph[k], &exec[k])) return s;
+        g_grid = g.grid;
+        g_det = g.det_grid;
+        g_block = g.block;
+        return PGC_OK;
+    }
+
+    pgc_status build_one_graph(const Geometry& g, bool setup, cudaGraph_t* graph_out,
+                               cudaGraphExec_t* exec_out) {
         Problem<V>* dP = problem.as<Problem<V>>();
-        PGC_CUDA(cudaGraphCreate(&graph, 0));
+        PGC_CUDA(cudaGraphCreate(graph_out, 0));
+        cudaGraph_t graph = *graph_out;
+        cudaGraphConditionalHandle handle = 0;
         PGC_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 0u, cudaGraphCondAssignDefault));
         int use_cond = 1;
         cudaGraphConditionalHandle hnd = handle;
+        int lo = 0, hi = INT32_MAX;
         void* p_args[] = {&dP};
+        void* b_args[] = {&dP, &lo, &hi};
         void* c_args[] = {&dP, &hnd, &use_cond};
         cudaMemsetParams ms = {};
         ms.dst = state.ptr;
@@ -1454,18 +1500,22 @@ struct Engine {
         ms.width = sizeof(State) / 4;
         ms.height = 1;
         cudaGraphNode_t n_ms, n_cls, n_build, n_tier, n_det, n_push, n_loop;
-        PGC_CUDA(cudaGraphAddMemsetNode(&n_ms, graph, nullptr, 0, &ms));
+        if (setup) PGC_CUDA(cudaGraphAddMemsetNode(&n_ms, graph, nullptr, 0, &ms));
         cudaKernelNodeParams k_cls = knode((void*)d1_classify<V>, g, g.smem, p_args);
-        cudaKernelNodeParams k_build = knode((void*)d1_build<V>, g, 0, p_args);
+        cudaKernelNodeParams k_build = knode((void*)d1_build<V>, g, 0, b_args);
         cudaKernelNodeParams k_tier = knode((void*)d1_tier<V>, g, g.smem, p_args);
         cudaKernelNodeParams k_det = knode((void*)d1_detect<V>, g, g.smem, c_args);
         k_det.gridDim = dim3(g.det_grid);
         cudaKernelNodeParams k_push = knode((void*)d1_push<V>, g, 0, p_args);
         cudaKernelNodeParams k_asg = knode((void*)d1_assign<V>, g, 0, c_args);
-        PGC_CUDA(cudaGraphAddKernelNode(&n_cls, graph, &n_ms, 1, &k_cls));
-        PGC_CUDA(cudaGraphAddKernelNode(&n_build, graph, &n_cls, 1, &k_build));
-        PGC_CUDA(cudaGraphAddKernelNode(&n_tier, graph, &n_build, 1, &k_tier));
-        PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, &n_tier, 1, &k_det));
+        if (setup) {
+            PGC_CUDA(cudaGraphAddKernelNode(&n_cls, graph, &n_ms, 1, &k_cls));
+            PGC_CUDA(cudaGraphAddKernelNode(&n_build, graph, &n_cls, 1, &k_build));
+            PGC_CUDA(cudaGraphAddKernelNode(&n_tier, graph, &n_build, 1, &k_tier));
+            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, &n_tier, 1, &k_det));
+        } else {
+            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, nullptr, 0, &k_det));
+        }
         PGC_CUDA(cudaGraphAddKernelNode(&n_push, graph, &n_det, 1, &k_push));
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
@@ -1496,10 +1546,7 @@ struct Engine {
         cudaLaunchAttributeValue coop = {};
         coop.cooperative = 1;
         PGC_CUDA(cudaGraphKernelNodeSetAttribute(n_cloop, cudaLaunchAttributeCooperative, &coop));
-        PGC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        g_grid = g.grid;
-        g_det = g.det_grid;
-        g_block = g.block;
+        PGC_CUDA(cudaGraphInstantiate(exec_out, graph, 0));
         return PGC_OK;
     }
 
@@ -1507,7 +1554,7 @@ struct Engine {
     // with scratch owned by this engine; waits for the result.
     pgc_status run(const V& view, int n, long long nnz, int* d_col, int* g_rounds,
                    int* g_colors, uint64_t seed, const Opts& o, cudaStream_t stream,
-                   int* rounds, int* num_colors) {
+                   int* rounds, int* num_colors, const Upload* up = nullptr) {
         // scratch grows, never shrinks; pointers travel in the Problem struct,
         // so the captured graph stays valid across calls
         const ScratchSizes z = scratch_sizes(n, nnz);
@@ -1534,7 +1581,8 @@ struct Engine {
         sc.wl = wl.as<int4>();
         sc.items = items.as<int2>();
         sc.pushq = pushq.as<int2>();
-        if (pgc_status s = launch(sc, view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream))
+        if (pgc_status s = launch(sc, view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream,
+                                  up))
             return s;
         PGC_CUDA(cudaStreamSynchronize(stream));
         return finish(o, rounds, num_colors);
@@ -1546,7 +1594,7 @@ struct Engine {
     // host memory on the same stream; call finish() once the stream is done.
     pgc_status launch(const Scratch& sc, const V& view, int n, long long nnz, int* d_col,
                       int* g_rounds, int* g_colors, uint64_t seed, const Opts& o,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, const Upload* up = nullptr) {
         if (pgc_status s = state.ensure(sizeof(State))) return s;
         if (pgc_status s = problem.ensure(sizeof(Problem<V>))) return s;
         if (pgc_status s = h_problem.ensure(sizeof(Problem<V>))) return s;
@@ -1603,10 +1651,47 @@ struct Engine {
 
         State* hs = h_state.as<State>();
         if (!(o.flags & PGC_HOST_LOOP)) {
-            if (!exec || g_grid != g.grid || g_block != g.block || g_det != g.det_grid) {
+            if (!exec[0] || g_grid != g.grid || g_block != g.block || g_det != g.det_grid) {
                 if (pgc_status s = build_graph(g)) return s;
             }
-            PGC_CUDA(cudaGraphLaunch(exec, stream));
+            if (!up) {
+                PGC_CUDA(cudaGraphLaunch(exec[0], stream));
+            } else {
+                // setup by hand: classify needs only the row offsets; the
+                // build of row range k waits for that range's copy
+                if (!up_stream) {
+                    PGC_CUDA(cudaStreamCreateWithFlags(&up_stream, cudaStreamNonBlocking));
+                    PGC_CUDA(cudaEventCreateWithFlags(&up_fork, cudaEventDisableTiming));
+                    for (cudaEvent_t& e : up_done)
+                        PGC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                }
+                int cut[kUploadChunks + 1];
+                cut[0] = 0;
+                cut[kUploadChunks] = n;
+                for (int k = 1; k < kUploadChunks; ++k) {   // first row past k/K of the entries
+                    const long long want = nnz * k / kUploadChunks;
+                    cut[k] = (int)(std::lower_bound(up->h_rp, up->h_rp + n, (int)want) - up->h_rp);
+                    cut[k] = std::max(cut[k], cut[k - 1]);
+                }
+                PGC_CUDA(cudaEventRecord(up_fork, stream));
+                PGC_CUDA(cudaStreamWaitEvent(up_stream, up_fork, 0));
+                for (int k = 0; k < kUploadChunks; ++k) {
+                    const size_t e0 = (size_t)up->h_rp[cut[k]], e1 = (size_t)up->h_rp[cut[k + 1]];
+                    if (e1 > e0)
+                        PGC_CUDA(cudaMemcpyAsync(up->d_ci + e0, up->h_ci + e0, (e1 - e0) * 4,
+                                                 cudaMemcpyHostToDevice, up_stream));
+                    PGC_CUDA(cudaEventRecord(up_done[k], up_stream));
+                }
+                PGC_CUDA(cudaMemsetAsync(state.ptr, 0, sizeof(State), stream));
+                d1_classify<V><<<g.grid, g.block, g.smem, stream>>>(dP);
+                for (int k = 0; k < kUploadChunks; ++k) {
+                    PGC_CUDA(cudaStreamWaitEvent(stream, up_done[k], 0));
+                    d1_build<V><<<g.grid, g.block, 0, stream>>>(dP, cut[k], cut[k + 1]);
+                }
+                d1_tier<V><<<g.grid, g.block, g.smem, stream>>>(dP);
+                PGC_CUDA(cudaGetLastError());
+                PGC_CUDA(cudaGraphLaunch(exec[1], stream));
+            }
         } else {
             KernelTimer kt;
             kt.prof = o.profile;
@@ -1621,7 +1706,8 @@ struct Engine {
         if (pgc_status s_ = kt.end()) return s_;              \
     } while (0)
             PGC_TIMED(0, "d1_classify", (d1_classify<V><<<g.grid, g.block, g.smem, stream>>>(dP)));
-            PGC_TIMED(1, "d1_build", (d1_build<V><<<g.grid, g.block, 0, stream>>>(dP)));
+            PGC_TIMED(1, "d1_build",
+                      (d1_build<V><<<g.grid, g.block, 0, stream>>>(dP, 0, INT32_MAX)));
             PGC_TIMED(2, "d1_tier", (d1_tier<V><<<g.grid, g.block, g.smem, stream>>>(dP)));
             for (int round = 1;; ++round) {
                 if (round > 1)

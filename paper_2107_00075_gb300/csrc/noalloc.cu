@@ -141,7 +141,7 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
     const size_t smem = (size_t)(block / 32) * 2 * kAppend4Slots * sizeof(int4);
     const cudaGraphConditionalHandle none = 0;
     d1_classify<SingleView><<<grid, block, smem, stream>>>(dP);
-    d1_build<SingleView><<<grid, block, 0, stream>>>(dP);
+    d1_build<SingleView><<<grid, block, 0, stream>>>(dP, 0, INT32_MAX);
     d1_tier<SingleView><<<grid, block, smem, stream>>>(dP);
     PGC_CUDA(cudaGetLastError());
     State hs;

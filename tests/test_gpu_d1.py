@@ -125,6 +125,27 @@ def test_pinned_host_arrays(pgc):
         assert r.rounds == want.rounds and r.num_colors == want.num_colors
 
 
+def test_large_host_arrays_overlapped_upload(pgc):
+    """A host adjacency of 2^24 entries or more is uploaded in row ranges
+    that overlap the list build; colors and rounds must equal those of the
+    same graph given in device memory, from pinned and from pageable host
+    memory, with the device loop and with the host-driven loop."""
+    import torch
+    g = gen.rmat(20, 16, seed=13)
+    assert g.nnz >= 1 << 24
+    dev = pgc.pgc_color_d1(torch.from_numpy(g.row_ptr).cuda(),
+                           torch.from_numpy(g.col_idx).cuda(), seed=2)
+    want = dev.colors.cpu().numpy()
+    rp = torch.from_numpy(g.row_ptr).pin_memory()
+    ci = torch.from_numpy(g.col_idx).pin_memory()
+    for args, flags in (((rp, ci), 0), ((rp, ci), 0), ((g.row_ptr, g.col_idx), 0),
+                        ((rp, ci), pgc.PGC_HOST_LOOP)):
+        r = pgc.pgc_color_d1(*args, seed=2, flags=flags)
+        got = r.colors.numpy() if hasattr(r.colors, "numpy") else r.colors
+        assert np.array_equal(got, want) and r.rounds == dev.rounds, flags
+    assert oracle.count_improper(oracle.D1, g.row_ptr, g.col_idx, want) == 0
+
+
 def test_edge_cases(pgc):
     import torch
     # n = 0
