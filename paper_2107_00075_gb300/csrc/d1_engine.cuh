@@ -902,7 +902,7 @@ __device__ __forceinline__ bool grid_barrier(State* st) {
 // per-vertex arrays in the other parity's worklist buffers (3 x 16n bytes).
 
 constexpr int kCoreBlocks = 32;
-constexpr int kUploadChunks = 4;    // host adjacency uploaded in this many row ranges
+constexpr int kUploadChunks = 8;    // host adjacency uploaded in this many row ranges
 
 // Adjacency still in (pinned) host memory when a coloring starts: it is
 // copied in kUploadChunks row ranges on a second stream, and the list build
