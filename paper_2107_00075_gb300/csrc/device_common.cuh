@@ -49,7 +49,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // with one atomicAdd, so list writes are coalesced and the list counter --
 // one address that every warp of the grid hits -- takes kAppendFlush times
 // fewer atomics.  All 32 lanes must call wa_push / wa_flush together.
-constexpr int kAppendFlush = 96;                // a multiple of 32
+constexpr int kAppendFlush = 224;               // a multiple of 32
 constexpr int kAppendSlots = kAppendFlush + 32; // per appender
 
 struct WarpAppend {

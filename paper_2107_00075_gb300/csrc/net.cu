@@ -653,6 +653,11 @@ static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
     g->block = o.block;
     g->smem = (size_t)(o.block / 32) * 2 * kAppendSlots * sizeof(int);
     g->det_smem = (size_t)(o.block / 32) * kDetSmemInts * sizeof(int);
+    if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
+        for (const void* f : {(const void*)net_init, (const void*)net_commit})
+            PGC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)g->smem));
+    }
     int per_sm = o.grid_per_sm;
     if (per_sm == 0) {
         int a = 0, b = 0;
