@@ -204,7 +204,7 @@ pgc_status pgc_color_d1_batch(int32_t G, const int64_t *vtx_off, const int64_t *
  * allocator, or who cannot accept the device-wide synchronisation of
  * cudaFree, get the same colors, rounds and color count as pgc_color_d1 with
  * no cudaMalloc, cudaFree or other allocating call.  All scratch is one
- * fixed array of about 4 MB in device memory that every GPU loading the
+ * fixed array of about 6.5 MB in device memory that every GPU loading the
  * library keeps until the process exits.
  *   Limits: n <= 32768 and row_ptr[n] <= 524288; larger inputs are rejected
  *           with PGC_ERR_INVALID_ARG before any work is launched.

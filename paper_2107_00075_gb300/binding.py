@@ -107,6 +107,9 @@ def lib():
         L.pgc_color_d1_batch.argtypes = [i32, p, p, p, p, u64, p, p, p, ctypes.POINTER(i32),
                                          ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_d1_batch.restype = ctypes.c_int
+        L.pgc_color_d1_noalloc.argtypes = [i32, p, p, u64, p, ctypes.POINTER(i32),
+                                           ctypes.POINTER(i32), ctypes.c_uint32, p]
+        L.pgc_color_d1_noalloc.restype = ctypes.c_int
         L.pgc_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(p)]
         L.pgc_server_create.restype = ctypes.c_int
         L.pgc_server_submit_d1.argtypes = [p, i32, p, p, u64, p, ctypes.POINTER(ctypes.c_int64)]
@@ -308,6 +311,32 @@ def _color_sym(fname, row_ptr, col_idx, seed, colors, flags, max_rounds, mid_deg
                                 ctypes.byref(o), _stream_handle(stream, dev))
     _check(st)
     _finish_profile(profile, keep, rounds.value)
+    return ColorResult(colors, rounds.value, ncol.value)
+
+
+def pgc_color_d1_noalloc(row_ptr, col_idx, seed: int = 1, colors=None, *, flags: int = 0,
+                         stream=None) -> ColorResult:
+    """Distance-1 coloring with no device allocation by the library (see
+    pgc.h): CUDA tensors only, n <= 32768 and nnz <= 524288.  With colors
+    None the output tensor is allocated here, by torch, before the call."""
+    rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
+    n = rp.n - 1
+    if n < 0:
+        raise ValueError("row_ptr must have n + 1 >= 1 entries")
+    if rp.device is None:
+        raise TypeError("pgc_color_d1_noalloc takes CUDA tensors only")
+    if colors is None:
+        colors = _alloc_colors(n, rp.device)
+    co = _Arr(colors, "colors")
+    if co.n < n:
+        raise ValueError("colors is shorter than n")
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    with _device_ctx(rp.device):
+        st = lib().pgc_color_d1_noalloc(n, rp.ptr, ci.ptr if ci.n else None,
+                                        ctypes.c_uint64(seed), co.ptr, ctypes.byref(rounds),
+                                        ctypes.byref(ncol), flags,
+                                        _stream_handle(stream, rp.device))
+    _check(st)
     return ColorResult(colors, rounds.value, ncol.value)
 
 

@@ -42,7 +42,7 @@ struct NoAllocLayout {
     static constexpr size_t total = align256(trace + 3 * sizeof(long long));
 };
 
-// The scratch itself (about 7 MB).  In host code this name is only a
+// The scratch itself (about 6.5 MB).  In host code this name is only a
 // stand-in for the device object; its device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
