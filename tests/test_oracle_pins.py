@@ -177,6 +177,87 @@ def test_path_and_odd_cycle_counts():
         assert oracle.count_improper(oracle.D1, g.row_ptr, g.col_idx, r.colors) == 0
 
 
+def _rank_colors(vertices, seed, first=1):
+    """Colors first, first+1, ... in increasing (rand, id) order: what a
+    clique of equal-degree vertices gets, one survivor per round."""
+    return {v: first + i for i, v in enumerate(sorted(vertices, key=lambda v: (h(v, seed), v)))}
+
+
+@pytest.mark.parametrize("leaves", [1, 2, 5, 17])
+@pytest.mark.parametrize("degree_rule", [True, False])
+def test_d2_star(leaves, degree_rule):
+    """D2 on K_{1,n}: every pair is within two hops, a clique of n + 1.  With
+    the degree rule the center (degree n) is colored 1 in round 1 and the
+    leaves follow one per round in (rand, id) order; without it all n + 1
+    vertices go in (rand, id) order.  Either way n + 1 rounds."""
+    g = gen.star(leaves)
+    seed = 3 + leaves
+    r = oracle.color_d2(g.row_ptr, g.col_idx, seed=seed, recolor_degrees=degree_rule)
+    if degree_rule and leaves >= 2:
+        want = {0: 1, **_rank_colors(range(1, leaves + 1), seed, first=2)}
+    else:     # one leaf: both vertices have degree 1, so only rand decides
+        want = _rank_colors(range(leaves + 1), seed)
+    assert list(r.colors) == [want[v] for v in range(leaves + 1)]
+    assert r.rounds == leaves + 1 and r.num_colors == leaves + 1
+    assert list(r.trace_w) == list(range(leaves + 1, 0, -1))
+
+
+@pytest.mark.parametrize("m,n", [(1, 3), (2, 5), (3, 4), (4, 4)])
+def test_d2_complete_bipartite(m, n):
+    """D2 on K_{m,n}: a clique of m + n.  For m < n the m side has the larger
+    degree, so it takes colors 1..m (by rand) before the n side takes
+    m+1..m+n; for m = n all degrees tie and rand alone orders them."""
+    g = gen.complete_bipartite(m, n)
+    r = oracle.color_d2(g.row_ptr, g.col_idx, seed=21)
+    if m < n:
+        want = {**_rank_colors(range(m), 21), **_rank_colors(range(m, m + n), 21, first=m + 1)}
+    else:
+        want = _rank_colors(range(m + n), 21)
+    assert list(r.colors) == [want[v] for v in range(m + n)]
+    assert r.rounds == m + n
+
+
+@pytest.mark.parametrize("sizes", [[1], [7], [3, 1, 4, 1, 5], [2, 2, 2, 9]])
+def test_pd2_disjoint_rows(sizes):
+    """PD2 where rows partition the columns: every column has degree 1 and
+    conflicts only inside its row, so each row is an independent clique:
+    its columns get 1..|row| in (rand, id) order, all rows in parallel, and
+    round r's worklist holds the columns of rank >= r of every row."""
+    seed = 5
+    rows, c = [], 0
+    for s in sizes:
+        rows.append(list(range(c, c + s)))
+        c += s
+    # shuffle column ids across rows so a row is not a contiguous id range
+    perm = np.random.default_rng(len(sizes)).permutation(c)
+    rows = [sorted(int(perm[x]) for x in row) for row in rows]
+    b = _graphs.bipartite_from_rows(rows, c)
+    r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                         seed=seed)
+    want = {}
+    for row in rows:
+        want.update(_rank_colors(row, seed))
+    assert list(r.colors) == [want[v] for v in range(c)]
+    assert r.rounds == max(sizes) and r.num_colors == max(sizes)
+    assert list(r.trace_w) == [sum(max(s - k, 0) for s in sizes) for k in range(max(sizes))]
+
+
+def test_pd2_hub_column_first():
+    """PD2 with one column in every row and the others in one row each: the
+    hub column has the largest degree, so it is colored 1 in round 1; within
+    each row the remaining columns take 2, 3, ... in (rand, id) order."""
+    seed = 8
+    rows = [[0, 1, 2, 3], [0, 4, 5], [0, 6]]
+    b = _graphs.bipartite_from_rows(rows, 7)
+    r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                         seed=seed)
+    want = {0: 1}
+    for row in rows:
+        want.update(_rank_colors(row[1:], seed, first=2))
+    assert list(r.colors) == [want[v] for v in range(7)]
+    assert r.rounds == 4
+
+
 # ------------------------------------------------------------- invariants ---
 def _random_graphs():
     out = []
