@@ -404,7 +404,7 @@ def _all_graphs(n):
         yield gen.from_edge_list(n, [p for j, p in enumerate(pairs) if mask >> j & 1])
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
 def test_exhaustive_small_graphs_match_set_version(n):
     for g in _all_graphs(n):
         for kind, f in (("d1", oracle.color_d1), ("d2", oracle.color_d2)):
@@ -413,6 +413,24 @@ def test_exhaustive_small_graphs_match_set_version(n):
                 c, rounds, k, sizes = setbased.color(kind, g.row_ptr, g.col_idx, n, rd)
                 assert list(r.colors) == c and r.rounds == rounds and r.num_colors == k
                 assert list(r.trace_w) == sizes
+
+
+@pytest.mark.parametrize("n_rows,n_cols", [(1, 4), (2, 3), (2, 5), (3, 3), (3, 4), (4, 3)])
+def test_exhaustive_small_patterns_match_set_version(n_rows, n_cols):
+    """Every rows x columns pattern of the given shape (all 2^(rows*cols)
+    of them), with and without the degree rule."""
+    cells = [(r, c) for r in range(n_rows) for c in range(n_cols)]
+    for mask in range(1 << len(cells)):
+        rows = [[c for (r2, c) in cells if r2 == r and mask >> cells.index((r2, c)) & 1]
+                for r in range(n_rows)]
+        b = _graphs.bipartite_from_rows(rows, n_cols)
+        for rd in (True, False):
+            r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr,
+                                 b.row_idx, seed=mask + 1, recolor_degrees=rd)
+            c, rounds, k, sizes = setbased.color("pd2", b.row_ptr, b.col_idx, mask + 1, rd,
+                                                 b.col_ptr, b.row_idx)
+            assert list(r.colors) == c and r.rounds == rounds and r.num_colors == k
+            assert list(r.trace_w) == sizes
 
 
 def test_random_graphs_match_set_version():
