@@ -42,20 +42,25 @@ def log(*a):
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
+    """Samples nvidia-smi every 100 ms in a background thread.  mark() and
+    unmark() bracket the timed region; only samples taken inside it count
+    toward the reported median clock and throttle reasons."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, exe: str = "nvidia-smi"):
         self.gpu = gpu_index
+        self.exe = exe
         self.proc = None
-        self.lines = []
+        self.lines = []          # (monotonic time, line)
         self.t = None
+        self.window = [None, None]
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                [self.exe, f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
@@ -66,7 +71,20 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_first(self, timeout: float = 3.0):
+        """Block until the first sample has arrived (or timeout), so that
+        the timed region that follows is sampled from its start."""
+        end = time.monotonic() + timeout
+        while self.proc is not None and not self.lines and time.monotonic() < end:
+            time.sleep(0.02)
+
+    def mark(self):
+        self.window[0] = time.monotonic()
+
+    def unmark(self):
+        self.window[1] = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -78,23 +96,42 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            p = [x.strip() for x in l.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                smax.append(float(p[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, p[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        t0, t1 = self.window
+        inside = [l for t, l in self.lines
+                  if (t0 is None or t >= t0) and (t1 is None or t <= t1)]
+        out = summarize_clocks(inside)
+        if not out["samples"]:
+            # a timed region shorter than the sampling period: fall back to
+            # every sample of the run, and say so
+            out = summarize_clocks([l for _, l in self.lines])
+            out["window"] = "whole run (no sample inside the timed region)"
+        else:
+            out["window"] = "timed region"
+        return out
+
+
+THROTTLE_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def summarize_clocks(lines):
+    """Median and max SM clock and the throttle reasons seen in nvidia-smi
+    CSV lines of ClockSampler.FIELDS (noheader, nounits)."""
+    sm, smax, reasons = [], [], set()
+    for l in lines:
+        p = [x.strip() for x in l.split(",")]
+        if len(p) < 9:
+            continue
+        try:
+            sm.append(float(p[1]))
+            smax.append(float(p[2]))
+        except ValueError:
+            continue
+        for name, val in zip(THROTTLE_NAMES, p[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # --------------------------------------------------------------------------
@@ -546,15 +583,17 @@ def main():
     # ---- device-timed steps (inputs resident; 2.1 GB CSR > L2) ----
     sampler = ClockSampler(local_rank)
     sampler.start()
-    time.sleep(0.3)
+    sampler.wait_first()
     barrier()
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    sampler.unmark()
     barrier()
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)

@@ -62,3 +62,50 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
     assert np.isclose(line["e2e"]["value"], line["value"])
+
+
+def test_summarize_clocks_parses_reasons():
+    lines = ["0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2070, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 1800, 2070, 1300.0, 0x8, Active, Not Active, Not Active, Not Active",
+             "garbage line", "0, [N/A], 2070, 1, 0, a, b, c, d"]
+    out = bench.summarize_clocks(lines)
+    assert out["samples"] == 3 and out["sm_mhz"] == 1965 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_keeps_only_the_timed_region(tmp_path):
+    """A fake nvidia-smi prints an idle clock before the timed region and a
+    loaded clock during it; the sampler must report the loaded one."""
+    flag = tmp_path / "loaded"
+    fake = tmp_path / "fake-smi"
+    fake.write_text(
+        "#!/bin/sh\n"
+        "while true; do\n"
+        f"  if [ -e {flag} ]; then c=2070; r=Active; else c=345; r='Not Active'; fi\n"
+        "  echo \"0, $c, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, $r\"\n"
+        "  sleep 0.02\n"
+        "done\n")
+    fake.chmod(0o755)
+    s = bench.ClockSampler(0, exe=str(fake))
+    s.start()
+    s.wait_first()
+    import time
+    time.sleep(0.2)            # idle samples before the timed region
+    flag.write_text("1")
+    time.sleep(0.1)
+    s.mark()
+    time.sleep(0.3)            # the "timed region"
+    s.unmark()
+    flag.unlink()
+    time.sleep(0.2)            # idle samples after it
+    out = s.stop()
+    assert out["window"] == "timed region" and out["samples"] >= 3
+    assert out["sm_mhz"] == 2070 and out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi():
+    s = bench.ClockSampler(0, exe="/nonexistent/nvidia-smi")
+    s.start()
+    s.wait_first(0.1)
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
