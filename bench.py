@@ -43,9 +43,11 @@ def log(*a):
 # --------------------------------------------------------------------------
 class ClockSampler:
     """Samples nvidia-smi every 100 ms in a background thread.  mark() and
-    unmark() bracket the timed region; only samples taken inside it count
-    toward the reported median clock and throttle reasons."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    unmark() bracket the timed region; only samples whose own timestamp
+    falls inside it count toward the reported median clock and throttle
+    reasons (nvidia-smi may buffer its output, so arrival time is used only
+    when a line's timestamp cannot be read)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -53,7 +55,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.exe = exe
         self.proc = None
-        self.lines = []          # (monotonic time, line)
+        self.lines = []          # (arrival time.time(), line)
         self.t = None
         self.window = [None, None]
 
@@ -71,20 +73,19 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append((time.monotonic(), line.strip()))
+            self.lines.append((time.time(), line.strip()))
 
     def wait_first(self, timeout: float = 3.0):
-        """Block until the first sample has arrived (or timeout), so that
-        the timed region that follows is sampled from its start."""
+        """Block until the first sample has arrived (or timeout)."""
         end = time.monotonic() + timeout
         while self.proc is not None and not self.lines and time.monotonic() < end:
             time.sleep(0.02)
 
     def mark(self):
-        self.window[0] = time.monotonic()
+        self.window[0] = time.time()
 
     def unmark(self):
-        self.window[1] = time.monotonic()
+        self.window[1] = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -97,12 +98,16 @@ class ClockSampler:
         if self.t:
             self.t.join(timeout=2)
         t0, t1 = self.window
-        inside = [l for t, l in self.lines
-                  if (t0 is None or t >= t0) and (t1 is None or t <= t1)]
+        inside = []
+        for arrived, line in self.lines:
+            t = sample_time(line)
+            t = arrived if t is None else t
+            if (t0 is None or t >= t0) and (t1 is None or t <= t1):
+                inside.append(line)
         out = summarize_clocks(inside)
         if not out["samples"]:
-            # a timed region shorter than the sampling period: fall back to
-            # every sample of the run, and say so
+            # a timed region shorter than the sampling period: report every
+            # sample of the run, and say so
             out = summarize_clocks([l for _, l in self.lines])
             out["window"] = "whole run (no sample inside the timed region)"
         else:
@@ -113,20 +118,31 @@ class ClockSampler:
 THROTTLE_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
 
+def sample_time(line):
+    """Seconds since the epoch of a ClockSampler line's timestamp field
+    (nvidia-smi prints local time as YYYY/MM/DD HH:MM:SS.mmm), or None."""
+    import datetime
+    try:
+        return datetime.datetime.strptime(line.split(",")[0].strip(),
+                                          "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
+
+
 def summarize_clocks(lines):
     """Median and max SM clock and the throttle reasons seen in nvidia-smi
     CSV lines of ClockSampler.FIELDS (noheader, nounits)."""
     sm, smax, reasons = [], [], set()
     for l in lines:
         p = [x.strip() for x in l.split(",")]
-        if len(p) < 9:
+        if len(p) < 10:
             continue
         try:
-            sm.append(float(p[1]))
-            smax.append(float(p[2]))
+            sm.append(float(p[2]))
+            smax.append(float(p[3]))
         except ValueError:
             continue
-        for name, val in zip(THROTTLE_NAMES, p[5:9]):
+        for name, val in zip(THROTTLE_NAMES, p[6:10]):
             if val.lower().startswith("active"):
                 reasons.add(name)
     return {"sm_mhz": statistics.median(sm) if sm else None,

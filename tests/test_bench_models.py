@@ -65,32 +65,48 @@ def test_reference_arm_json_line():
 
 
 def test_summarize_clocks_parses_reasons():
-    lines = ["0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
-             "0, 2070, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
-             "0, 1800, 2070, 1300.0, 0x8, Active, Not Active, Not Active, Not Active",
-             "garbage line", "0, [N/A], 2070, 1, 0, a, b, c, d"]
+    ts = "2026/12/04 01:02:03.456"
+    lines = [f"{ts}, 0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             f"{ts}, 0, 2070, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+             f"{ts}, 0, 1800, 2070, 1300.0, 0x8, Active, Not Active, Not Active, Not Active",
+             "garbage line", f"{ts}, 0, [N/A], 2070, 1, 0, a, b, c, d"]
     out = bench.summarize_clocks(lines)
     assert out["samples"] == 3 and out["sm_mhz"] == 1965 and out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    import datetime
+    want = datetime.datetime(2026, 12, 4, 1, 2, 3, 456000).timestamp()
+    assert abs(bench.sample_time(lines[0]) - want) < 1e-6
+    assert bench.sample_time("garbage line") is None
 
 
-def test_clock_sampler_keeps_only_the_timed_region(tmp_path):
-    """A fake nvidia-smi prints an idle clock before the timed region and a
-    loaded clock during it; the sampler must report the loaded one."""
-    flag = tmp_path / "loaded"
+def _fake_smi(tmp_path, flag, buffered):
+    """A stand-in for nvidia-smi: an idle clock normally, a loaded clock with
+    sw_power_cap while flag exists; buffered=True holds every line until exit
+    (as a block-buffered pipe could), so only the timestamps place them."""
     fake = tmp_path / "fake-smi"
+    out = tmp_path / "held.txt"
+    emit = f">> {out}" if buffered else ""
+    trap = f"trap 'cat {out}; exit 0' TERM\n" if buffered else ""
     fake.write_text(
-        "#!/bin/sh\n"
+        "#!/bin/bash\n" + trap +
         "while true; do\n"
         f"  if [ -e {flag} ]; then c=2070; r=Active; else c=345; r='Not Active'; fi\n"
-        "  echo \"0, $c, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, $r\"\n"
+        "  ts=$(date '+%Y/%m/%d %H:%M:%S.%3N')\n"
+        f"  echo \"$ts, 0, $c, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, $r\" {emit}\n"
         "  sleep 0.02\n"
         "done\n")
     fake.chmod(0o755)
-    s = bench.ClockSampler(0, exe=str(fake))
-    s.start()
-    s.wait_first()
+    return str(fake)
+
+
+@pytest.mark.parametrize("buffered", [False, True])
+def test_clock_sampler_keeps_only_the_timed_region(tmp_path, buffered):
+    """Idle samples before and after the timed region must not count."""
     import time
+    flag = tmp_path / "loaded"
+    s = bench.ClockSampler(0, exe=_fake_smi(tmp_path, flag, buffered))
+    s.start()
+    s.wait_first(0.5)
     time.sleep(0.2)            # idle samples before the timed region
     flag.write_text("1")
     time.sleep(0.1)
