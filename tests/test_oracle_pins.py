@@ -434,8 +434,10 @@ def test_exhaustive_small_patterns_match_set_version(n_rows, n_cols):
 
 
 def test_random_graphs_match_set_version():
+    """10^4 random cases with n <= 12: 8000 graphs (D1 and D2) and 2000
+    row x column patterns (PD2), seeds and the degree flag varied."""
     rng = np.random.default_rng(42)
-    for i in range(400):
+    for i in range(8000):
         n = int(rng.integers(1, 13))
         g = gen.random_small(n, float(rng.uniform(0.05, 0.9)), seed=int(rng.integers(1 << 30)))
         seed = int(rng.integers(1 << 62))
@@ -444,7 +446,7 @@ def test_random_graphs_match_set_version():
             r = f(g.row_ptr, g.col_idx, seed=seed, recolor_degrees=rd)
             c, rounds, k, sizes = setbased.color(kind, g.row_ptr, g.col_idx, seed, rd)
             assert list(r.colors) == c and r.rounds == rounds and list(r.trace_w) == sizes
-    for i in range(150):
+    for i in range(2000):
         b = gen.random_bipartite_small(int(rng.integers(1, 10)), int(rng.integers(1, 12)),
                                        float(rng.uniform(0.05, 0.6)), seed=i)
         seed = int(rng.integers(1 << 62))
