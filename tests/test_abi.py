@@ -71,3 +71,58 @@ def test_host_argument_checks_without_gpu():
                         ctypes.byref(o), None)
     assert st == 1
     assert b"block" in L.pgc_last_error()
+
+
+C_USER = r"""
+#include <stdio.h>
+#include "pgc.h"
+/* A C caller of every entry point family: compiled and linked, not run. */
+int use_all(const int32_t* rp, const int32_t* ci, const int32_t* cp, const int32_t* ri,
+            const int64_t* vo, const int64_t* no, int32_t* col) {
+    int32_t rounds = 0, ncol = 0, rpg = 0, cpg = 0, maxr = 0;
+    pgc_opts o;
+    pgc_opts_init(&o);
+    o.flags = PGC_NO_DEGREE_RULE | PGC_VALIDATE;
+    pgc_status s = pgc_color_d1(4, rp, ci, 1u, col, &rounds, &ncol, &o, NULL);
+    s = pgc_color_d2(4, rp, ci, 1u, col, &rounds, &ncol, NULL, NULL);
+    s = pgc_color_pd2(3, 4, rp, ci, cp, ri, 1u, col, &rounds, &ncol, NULL, NULL);
+    s = pgc_color_d1_batch(1, vo, no, rp, ci, 1u, col, &rpg, &cpg, &maxr, NULL, NULL);
+    s = pgc_color_d1_noalloc(4, rp, ci, 1u, col, &rounds, &ncol, 0u, NULL);
+    pgc_server* srv = NULL;
+    int64_t id = 0;
+    pgc_request_info info;
+    if (pgc_server_create((size_t)1 << 30, 4, &srv) == PGC_OK) {
+        int32_t done = 0;
+        pgc_server_counters cnt;
+        pgc_server_submit_d1(srv, 4, rp, ci, 1u, col, &id);
+        pgc_server_poll(srv, id, &done, &info);
+        pgc_server_submit_pd2(srv, 3, 4, rp, ci, cp, ri, 1u, col, &id);
+        pgc_server_wait(srv, id, 1000, &info);
+        pgc_server_stats(srv, &cnt);
+        pgc_server_destroy(srv);
+    }
+    printf("%s %s %s\n", pgc_status_string(s), pgc_last_error(), pgc_version());
+    return (int)pgc_release();
+}
+int main(void) { return 0; }
+"""
+
+
+@pytest.mark.parametrize("lang", ["c99", "c11", "c++17"])
+def test_header_compiles_and_links_from_c(tmp_path, lang):
+    """include/pgc.h is plain C (no torch or CUDA types): a C or C++ caller
+    of every entry point compiles warning-free and links to libpgc.so."""
+    import shutil
+    import subprocess
+    cc = "g++" if lang.startswith("c++") else "gcc"
+    if shutil.which(cc) is None:
+        pytest.skip(f"{cc} not available")
+    lib = _native.build()
+    src = tmp_path / ("user.cpp" if cc == "g++" else "user.c")
+    src.write_text(C_USER)
+    exe = tmp_path / "user"
+    cmd = [cc, f"-std={lang}", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", HEADER_DIR,
+           str(src), "-o", str(exe), "-L", os.path.dirname(lib), "-lpgc",
+           f"-Wl,-rpath,{os.path.dirname(lib)}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
