@@ -44,6 +44,12 @@ MUTANTS = [
     ("pd2_degree_from_rows",
      "if (g->kind == KIND_PD2) return g->col_ptr[v + 1] - g->col_ptr[v];",
      "if (g->kind == KIND_PD2) return 1;"),
+    ("d2_one_hop_dropped",
+     "if (u != v) buf[k++] = u;                 /* one hop */",
+     "(void)u;"),
+    ("seed_added_not_xored",
+     "return oracle_splitmix64(seed ^ (uint64_t)(uint32_t)v);",
+     "return oracle_splitmix64(seed + (uint64_t)(uint32_t)v);"),
     ("winner_color_off_by_one",
      "committed[v] = tent[v];\n            }",
      "committed[v] = tent[v] + (tent[v] > 1);\n            }"),
