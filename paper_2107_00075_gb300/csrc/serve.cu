@@ -13,6 +13,7 @@
 // pgc_color_d1 / pgc_color_pd2 on the request alone: every request is
 // computed by its own instance of the same engine, with graph-local state.
 #include "d1_engine.cuh"
+#include "arena.h"
 
 #include <atomic>
 #include <chrono>
@@ -31,52 +32,6 @@ static long long now_ns() {
 }
 
 static size_t al(size_t x) { return (x + 255) / 256 * 256; }
-
-// First-fit allocator over [0, cap) with coalescing of free neighbours.
-class Arena {
-  public:
-    void init(size_t cap) {
-        cap_ = cap;
-        free_.clear();
-        if (cap) free_[0] = cap;
-        used_ = 0;
-    }
-    bool alloc(size_t bytes, size_t* off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto next = std::next(it);
-        if (next != free_.end() && it->first + it->second == next->first) {
-            it->second += next->second;
-            free_.erase(next);
-        }
-        if (it != free_.begin()) {
-            auto prev = std::prev(it);
-            if (prev->first + prev->second == it->first) {
-                prev->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-
-  private:
-    size_t cap_ = 0, used_ = 0;
-    std::map<size_t, size_t> free_;
-};
 
 enum Kind { KIND_D1 = 1, KIND_PD2 = 3 };
 
