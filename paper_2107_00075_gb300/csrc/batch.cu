@@ -10,6 +10,7 @@
 // a size class and reuses the fastest one afterwards; colors do not depend
 // on the choice.
 #include "d1_engine.cuh"
+#include "tune_cache.h"
 
 #include <cmath>
 #include <cstdio>
@@ -94,10 +95,6 @@ static BatchBufs& bufs_for(int device) {
 // autotuner: candidates, size classes, an in-memory cache mirrored to the
 // file named by PGC_TUNE_FILE (lines "key block mid hub")
 // --------------------------------------------------------------------------
-struct Tuned {
-    int block, mid, hub;
-};
-
 static std::mutex g_tune_mu;
 static std::map<std::string, Tuned>& tune_cache() {
     static std::map<std::string, Tuned> m;
@@ -106,10 +103,7 @@ static std::map<std::string, Tuned>& tune_cache() {
         loaded = true;
         if (const char* f = std::getenv("PGC_TUNE_FILE")) {
             if (FILE* fp = std::fopen(f, "r")) {
-                char key[128];
-                Tuned t;
-                while (std::fscanf(fp, "%127s %d %d %d", key, &t.block, &t.mid, &t.hub) == 4)
-                    m[key] = t;
+                tune_file_read(fp, m);
                 std::fclose(fp);
             }
         }
@@ -121,20 +115,10 @@ static void tune_store(const std::string& key, const Tuned& t) {
     tune_cache()[key] = t;
     if (const char* f = std::getenv("PGC_TUNE_FILE")) {
         if (FILE* fp = std::fopen(f, "a")) {
-            std::fprintf(fp, "%s %d %d %d\n", key.c_str(), t.block, t.mid, t.hub);
+            tune_file_append(fp, key, t);
             std::fclose(fp);
         }
     }
-}
-
-// Size class: log2 of the vertex count, of the mean degree and of the graph
-// count, plus the priority rule (it changes the detection lists).
-static std::string size_class(long long n, long long nnz, int G, bool use_deg) {
-    auto lg = [](double x) { return x <= 1 ? 0 : (int)std::lround(std::log2(x)); };
-    char buf[96];
-    std::snprintf(buf, sizeof buf, "d1b:n%d:d%d:g%d:r%d", lg((double)n),
-                  lg((double)nnz / std::max(1LL, n)), lg((double)G), use_deg ? 1 : 0);
-    return buf;
 }
 
 static pgc_status color_batch(int32_t G, const int64_t* vtx_off, const int64_t* nnz_off,
@@ -241,7 +225,7 @@ static pgc_status color_batch(int32_t G, const int64_t* vtx_off, const int64_t* 
 
     int rounds = 0, ncolors = 0;
     if (o.flags & PGC_AUTOTUNE) {
-        const std::string key = size_class(N, NNZ, G, !(o.flags & PGC_NO_DEGREE_RULE));
+        const std::string key = tune_size_class(N, NNZ, G, !(o.flags & PGC_NO_DEGREE_RULE));
         Tuned best{0, 0, 0};
         bool have = false;
         {
