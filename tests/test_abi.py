@@ -126,3 +126,37 @@ def test_header_compiles_and_links_from_c(tmp_path, lang):
            f"-Wl,-rpath,{os.path.dirname(lib)}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("max_rounds", -1, b"max_rounds"), ("mid_degree", -5, b"degree"),
+    ("hub_degree", -1, b"degree"), ("block", 96, b"block"), ("block", 2048, b"block"),
+    ("block", 200, b"block"), ("grid_per_sm", -2, b"grid_per_sm"),
+    ("timeout_ms", -1, b"timeout_ms")])
+def test_invalid_options_rejected_without_gpu(field, value, msg):
+    """Every entry point that takes pgc_opts checks it before any device
+    work: an empty problem with a bad option is INVALID_ARG with a message
+    naming the option, and with good options it is OK."""
+    L = binding.lib()
+    r, k = ctypes.c_int32(7), ctypes.c_int32(7)
+    o = binding.PgcOptsC()
+    L.pgc_opts_init(ctypes.byref(o))
+    setattr(o, field, value)
+    empty = (ctypes.c_int32 * 1)(0)
+    calls = {
+        "d1": lambda opts: L.pgc_color_d1(0, empty, None, 1, None, ctypes.byref(r),
+                                          ctypes.byref(k), opts, None),
+        "d2": lambda opts: L.pgc_color_d2(0, empty, None, 1, None, ctypes.byref(r),
+                                          ctypes.byref(k), opts, None),
+        "pd2": lambda opts: L.pgc_color_pd2(0, 0, empty, None, empty, None, 1, None,
+                                            ctypes.byref(r), ctypes.byref(k), opts, None),
+    }
+    for name, call in calls.items():
+        st = call(ctypes.byref(o))
+        assert st == 1, (name, st)
+        assert msg in L.pgc_last_error(), (name, L.pgc_last_error())
+        good = binding.PgcOptsC()
+        L.pgc_opts_init(ctypes.byref(good))
+        good.block, good.mid_degree, good.hub_degree = 512, 32, 1024
+        assert call(ctypes.byref(good)) == 0, name
+        assert call(None) == 0 and r.value == 0 and k.value == 0, name
