@@ -751,9 +751,9 @@ def main():
         # OpenMP's default wait policy spins at barriers (fast on idle
         # cores, slow if any core is busy); the passive one sleeps: keep the
         # faster of the two
-        runs = [x for x in (cpu_parallel_edges_per_s(args.cpu_baseline_scale,
+        runs = [x for x in (cpu_parallel_edges_per_s(args.cpu_baseline_scale, timeout=120.0,
                                                      wait_policy="PASSIVE"),
-                            cpu_parallel_edges_per_s(args.cpu_baseline_scale, timeout=90.0))
+                            cpu_parallel_edges_per_s(args.cpu_baseline_scale, timeout=60.0))
                 if x and (x["rounds"], x["num_colors"]) == (ores.rounds, ores.num_colors)]
         par = min(runs, key=lambda x: x["secs"]) if runs else None
         if par is not None:
