@@ -60,6 +60,17 @@ def col_idx_rows(col_ptr, row_idx, v):
 
 def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, row_idx=None):
     """Returns (colors, rounds, num_colors, worklist sizes per round)."""
+    colors, lists = _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx)
+    return colors, len(lists), max(colors, default=0), [len(w) for w in lists]
+
+
+def worklists(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None,
+              row_idx=None):
+    """The worklist W_r of every round r = 1, 2, ... as sorted vertex lists."""
+    return _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx)[1]
+
+
+def _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx):
     S = neighborhoods(kind, row_ptr, col_idx, col_ptr, row_idx)
     n = len(S)
     if kind == "pd2":
@@ -73,9 +84,9 @@ def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, ro
 
     final = {}
     todo = set(range(n))
-    sizes = []
+    lists = []
     while todo:
-        sizes.append(len(todo))
+        lists.append(sorted(todo))
         tentative = {}
         for v in todo:
             used = {final[u] for u in S[v] if u in final}
@@ -91,4 +102,4 @@ def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, ro
             final[v] = tentative[v]
         todo = losers
     colors = [final[v] for v in range(n)]
-    return colors, len(sizes), max(colors, default=0), sizes
+    return colors, lists

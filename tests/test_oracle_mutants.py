@@ -53,6 +53,21 @@ MUTANTS = [
     ("winner_color_off_by_one",
      "committed[v] = tent[v];\n            }",
      "committed[v] = tent[v] + (tent[v] > 1);\n            }"),
+    # the per-round degree sums (trace_s)
+    ("trace_s_over_next_worklist",
+     "int32_t *tmp = work; work = next; next = tmp;\n        wn = nn;",
+     "int32_t *tmp = work; work = next; next = tmp;\n        wn = nn;\n"
+     "        if (trace_w && r <= trace_cap) {\n"
+     "            int64_t s2 = 0;\n"
+     "            for (int32_t i = 0; i < wn; ++i) s2 += deg[work[i]];\n"
+     "            trace_s[r - 1] = s2;\n"
+     "        }"),
+    ("trace_s_neighborhood_size",
+     "for (int32_t i = 0; i < wn; ++i) s += deg[work[i]];",
+     "for (int32_t i = 0; i < wn; ++i) s += neighborhood(g, work[i], buf);"),
+    ("trace_s_skips_first_entry",
+     "for (int32_t i = 0; i < wn; ++i) s += deg[work[i]];",
+     "for (int32_t i = 1; i < wn; ++i) s += deg[work[i]];"),
 ]
 
 
@@ -77,6 +92,21 @@ def _pins_pass(lib) -> bool:
                       recolor_degrees=c["recolor_degrees"], lib=lib)
             if list(r.colors) != c["colors"] or r.rounds != c["rounds"]:
                 return False
+        # per-round degree sums: K_n, D2 on a star, PD2 with disjoint rows
+        for n in (2, 5, 9):
+            g = gen.complete(n)
+            r = oracle.color_d1(g.row_ptr, g.col_idx, seed=4, lib=lib)
+            if list(r.trace_s) != [(n - 1) * (n - k) for k in range(n)]:
+                return False
+        g = gen.star(6)
+        r = oracle.color_d2(g.row_ptr, g.col_idx, seed=9, lib=lib)
+        if list(r.trace_s) != [12, 6, 5, 4, 3, 2, 1]:
+            return False
+        b = _graphs.bipartite_from_rows([[0, 1, 2], [3, 4], [5]], 6)
+        r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                             seed=5, lib=lib)
+        if list(r.trace_s) != [6, 3, 1]:
+            return False
         # K_{m,n} closed form and the D2 = D1(G^2) reduction
         g = gen.complete_bipartite(3, 7)
         r = oracle.color_d1(g.row_ptr, g.col_idx, seed=7, lib=lib)

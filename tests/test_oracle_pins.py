@@ -498,3 +498,83 @@ def test_checkers_on_hand_colorings():
     assert oracle.count_improper(oracle.PD2, b.row_ptr, b.col_idx, [1, 1, 2], **kw) == 2
     assert oracle.count_non_grundy(oracle.PD2, b.row_ptr, b.col_idx, [2, 1, 2], **kw) == 0
     assert oracle.count_non_grundy(oracle.PD2, b.row_ptr, b.col_idx, [3, 1, 2], **kw) == 1  # column 0
+
+
+# ------------------------------------------- per-round degree sums (trace_s) ---
+# trace_s[r-1] is S_r = the sum of deg(v) over the worklist W_r of round r
+# (the degree of Sec. 3.3: row length for D1/D2, column length for PD2).
+# These pins fix it from closed forms, independently of the oracle's loop.
+@pytest.mark.parametrize("n", [1, 2, 5, 16])
+def test_trace_s_complete_graph(n):
+    """K_n: W_r holds n - r + 1 vertices, each of degree n - 1."""
+    g = gen.complete(n)
+    r = oracle.color_d1(g.row_ptr, g.col_idx, seed=4)
+    assert list(r.trace_s) == [(n - 1) * (n - k) for k in range(n)]
+
+
+@pytest.mark.parametrize("leaves", [2, 3, 10])
+def test_trace_s_star(leaves):
+    """Star K_{1,n}: round 1 holds every vertex (n + n * 1 = 2n), round 2 the
+    n leaves (degree 1 each)."""
+    g = gen.star(leaves)
+    r = oracle.color_d1(g.row_ptr, g.col_idx, seed=11)
+    assert list(r.trace_w) == [leaves + 1, leaves]
+    assert list(r.trace_s) == [2 * leaves, leaves]
+
+
+@pytest.mark.parametrize("m,n", [(1, 2), (3, 7), (5, 6)])
+def test_trace_s_complete_bipartite(m, n):
+    """K_{m,n}, m < n: round 1 all m + n vertices (2mn), round 2 the n side,
+    each of degree m."""
+    g = gen.complete_bipartite(m, n)
+    r = oracle.color_d1(g.row_ptr, g.col_idx, seed=7)
+    assert list(r.trace_s) == [2 * m * n, n * m]
+
+
+@pytest.mark.parametrize("leaves", [2, 5, 17])
+def test_trace_s_d2_star(leaves):
+    """D2 on K_{1,n} with the degree rule: round 1 holds all n + 1 vertices
+    (2n), then the leaves leave one per round; the sum is of 1-hop degrees
+    (1 per leaf), not of two-hop neighborhood sizes (n per leaf)."""
+    g = gen.star(leaves)
+    r = oracle.color_d2(g.row_ptr, g.col_idx, seed=3 + leaves)
+    assert list(r.trace_s) == [2 * leaves] + list(range(leaves, 0, -1))
+
+
+@pytest.mark.parametrize("sizes", [[7], [3, 1, 4, 1, 5]])
+def test_trace_s_pd2_disjoint_rows(sizes):
+    """PD2 with rows partitioning the columns: every column has degree 1, so
+    S_r = |W_r| = the columns of rank >= r within their row."""
+    rows, c = [], 0
+    for s in sizes:
+        rows.append(list(range(c, c + s)))
+        c += s
+    b = _graphs.bipartite_from_rows(rows, c)
+    r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                         seed=5)
+    want = [sum(max(s - k, 0) for s in sizes) for k in range(max(sizes))]
+    assert list(r.trace_s) == want
+
+
+def test_trace_s_pd2_hub_column():
+    """Hub column 0 in all three rows (degree 3) plus columns of degree 1: the
+    hub wins round 1, so S_1 = 3 + 6 and S_r = |W_r| afterwards."""
+    rows = [[0, 1, 2, 3], [0, 4, 5], [0, 6]]
+    b = _graphs.bipartite_from_rows(rows, 7)
+    r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                         seed=8)
+    assert r.trace_s[0] == 9
+    assert list(r.trace_s[1:]) == list(r.trace_w[1:])
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_trace_s_matches_set_version_worklists(i):
+    """On random graphs: the degree sum over each round's worklist, with the
+    worklists taken from the set-based restatement."""
+    g = gen.random_small(6 + i, 0.35, seed=300 + i)
+    deg = np.diff(g.row_ptr)
+    for kind, f in (("d1", oracle.color_d1), ("d2", oracle.color_d2)):
+        r = f(g.row_ptr, g.col_idx, seed=i + 2)
+        lists = setbased.worklists(kind, g.row_ptr, g.col_idx, i + 2, True)
+        assert list(r.trace_w) == [len(w) for w in lists]
+        assert list(r.trace_s) == [int(sum(deg[w])) for w in lists]
