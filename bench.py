@@ -153,46 +153,90 @@ def summarize_clocks(lines):
 # --------------------------------------------------------------------------
 # algorithmic bytes (per kernel, from the per-round trace)
 # --------------------------------------------------------------------------
-def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None):
-    """Bytes each kernel must move for one coloring (int32 ids and colors,
-    64-bit forbidden-color words), from the per-round trace: |W_r|,
-    S_r = sum of deg over W_r and H_r = sum of |H(v)| over W_r (the scan
-    lists).  Rounds from tail_at on run in the core phase (the subgraph
-    induced by the worklist), counted with the same per-round model.
-      classify: offsets 4(n+1) + degree, color, list-length writes 12n +
-                forbidden word 8n + worklist 4n (overflow-bitmap clears of
-                vertices with deg >= 64 not counted)
-      build:    worklist 4n + offsets 8n + adjacency 4 nnz + neighbor degree
-                4 nnz + H lists 4 H_1 + list lengths 4n
-      tier:     list lengths 4n + worklists 4n
-      assign (r >= 2): worklist 4 + forbidden word 8 + color write 4 = 16 |W_r|
-      detect:   worklist, offset, list length, own color, commit/append:
-                20 |W_r| + H entries and their colors 8 H_r (upper bound: a
-                loser stops at its first conflict)
-      push:     per adjacency entry of the round's winners (S_r - S_{r+1},
-                whether pushed inline by detect or by the push kernel):
-                neighbor id 4 + forbidden-word update 8 = 12 B
-    """
+def d1_setup_bytes(n, nnz, h1, deg=None, build_item=512, build_m=512):
+    """Bytes the three setup kernels move for one coloring (what the code
+    loads and stores, int32 ids, 16-byte worklist entries).  deg: the degree
+    array (for the overflow-bitmap clears and the long-row items), or None
+    to leave those terms out.
+      classify: offsets 4(n+1); degree, color and list-length writes 12n;
+                forbidden word 8n; uncolored bitmap n/8; a 16-byte entry for
+                every vertex of degree <= build_m and an 8-byte item per
+                build_item adjacency entries of longer rows; the overflow
+                bitmap of every vertex of degree >= 64 cleared, 4((d>>5)+1)
+      build:    the entries and items again; adjacency 4 nnz and the
+                neighbor's degree 4 nnz; the kept list entries 4 H_1 and the
+                list lengths 4n
+      tier:     list lengths 4n, offsets 4(n+1), entries 16n"""
+    n = float(n)
+    clears = items = 0.0
+    small = n
+    if deg is not None:
+        d = np.asarray(deg, dtype=np.int64)
+        big = d >= 64
+        clears = float((4 * ((d[big] >> 5) + 1)).sum())
+        long_rows = d > build_m
+        items = float(((d[long_rows] + build_item - 1) // build_item).sum())
+        small = float(n - long_rows.sum())
+    return {
+        "d1_classify": 4.0 * (n + 1) + 12.0 * n + 8.0 * n + n / 8.0 + 16.0 * small +
+                       8.0 * items + clears,
+        "d1_build": 16.0 * small + 8.0 * items + 8.0 * nnz + 4.0 * h1 + 4.0 * n,
+        "d1_tier": 4.0 * n + 4.0 * (n + 1) + 16.0 * n,
+    }
+
+
+def d1_round_bytes(trace_w, trace_s, trace_h):
+    """Per-round bytes of the three round kernels, from the trace (entry r-1
+    describes round r: |W_r|, S_r = sum of deg over W_r, H_r = sum of the
+    priority-list lengths over W_r).  Returns three arrays (one entry per
+    round).
+      assign (r >= 2): entry 16 + own color 4 + forbidden word 8 + color
+                write 4 = 32 per worklist vertex (overflow-bitmap words of
+                vertices past color 64 not counted)
+      detect:   entry 16 + own color 4 per worklist vertex; 8 per priority-list
+                entry (id + the neighbor's color; round 1 reads no list; an
+                upper bound, losers stop at their first conflict); per winner
+                a color write and an uncolored-bit update (8) and its push
+                items (8 per 128 adjacency entries); per loser its next-round
+                entry (16)
+      push:     per adjacency entry of the round's winners (S_r - S_{r+1}):
+                neighbor id 4 + its uncolored word 4 + forbidden-word update
+                8 = 16 (pushed by detect inline or by the push kernel)"""
     w = np.asarray(trace_w, dtype=np.float64)
     sw = np.asarray(trace_s, dtype=np.float64)
     hh = np.asarray(trace_h, dtype=np.float64)
+    wn = np.append(w[1:], 0.0)
+    won = w - wn
+    won_adj = sw - np.append(sw[1:], 0.0)
+    asg = 32.0 * w
+    if len(asg):
+        asg[0] = 0.0
+    lists = hh.copy()
+    if len(lists):
+        lists[0] = 0.0
+    det = 20.0 * w + 8.0 * lists + 8.0 * won + won_adj / 16.0 + 16.0 * wn
+    psh = 16.0 * won_adj
+    return asg, det, psh
+
+
+def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None, deg=None):
+    """Bytes each kernel moves for one coloring (d1_setup_bytes and
+    d1_round_bytes).  Rounds from tail_at on run in the core phase (the
+    subgraph induced by the worklist): the extraction reads the worklist's
+    adjacency twice (id, uncolored bit and degree: 12 per entry each time),
+    then its rounds are counted with the per-round model."""
+    w = np.asarray(trace_w, dtype=np.float64)
     R = len(w)
     t = R if tail_at is None else tail_at
-    won = sw - np.append(sw[1:], 0.0)
-    asg = 16 * w
-    asg[0] = 0.0
-    det = 20 * w + 8 * hh
-    psh = 12 * won
-    out = {
-        "d1_classify": 4.0 * (n + 1) + 24.0 * n,
-        "d1_build": 16.0 * n + 8.0 * nnz + 4.0 * float(hh[0]),
-        "d1_tier": 8.0 * n,
-        "d1_assign": float(asg[:t].sum()),
-        "d1_detect": float(det[:t].sum()),
-        "d1_push": float(psh[:t].sum()),
-    }
+    hh = np.asarray(trace_h, dtype=np.float64)
+    out = d1_setup_bytes(n, nnz, float(hh[0]) if R else 0.0, deg)
+    asg, det, psh = d1_round_bytes(trace_w, trace_s, trace_h)
+    out["d1_assign"] = float(asg[:t].sum())
+    out["d1_detect"] = float(det[:t].sum())
+    out["d1_push"] = float(psh[:t].sum())
     if t < R:
-        out["d1_core"] = float(asg[t:].sum() + det[t:].sum() + psh[t:].sum())
+        st = float(np.asarray(trace_s, dtype=np.float64)[t])
+        out["d1_core"] = 24.0 * st + float(asg[t:].sum() + det[t:].sum() + psh[t:].sum())
     return out
 
 
@@ -219,6 +263,45 @@ def d1_method_bytes(trace_w, trace_s, n, nnz, tail_at=None):
     return float(per[:t].sum()), t
 
 
+def net_algorithmic_bytes(trace_w, trace_h, trace_nets, trace_members, n, n_nets,
+                          members_total, windows=1):
+    """Bytes the D2/PD2 kernels move for one coloring, from the per-round
+    trace (entry r-1 describes round r: |W_r|; K_r = the nets of W_r's
+    vertices, counted with multiplicity; A_r, M_r = the nets detection visited
+    and their members).  A round marks nets only when it does not visit every
+    net.  Mask reads count one window (colors <= 64).
+      init:    per vertex offsets 8, key 8, color 4, lose flag 4, worklist 4;
+               per net of a vertex its id 4 and its size (two offsets) 8;
+               net flags 4 per net
+      assign:  per worklist vertex entry 4, offsets 8, color write 4; per net
+               of a worklist vertex its id 4 and mask word 8 (* windows),
+               and when marking its flag read and write 8
+      detect:  per visited net offsets 8 (and its flag 4 when marking); per
+               member id 4, color 4, key 8; a lose flag per loser 4
+      commit:  per worklist vertex entry 4, lose flag 4; per winner offsets 8,
+               color read and write 8, and per net of a winner its id 4 and
+               mask update 8; per loser its next-round entry 4"""
+    w = np.asarray(trace_w, dtype=np.float64)
+    k = np.asarray(trace_h, dtype=np.float64)
+    a = np.asarray(trace_nets, dtype=np.float64)
+    m = np.asarray(trace_members, dtype=np.float64)
+    wn = np.append(w[1:], 0.0)
+    kn = np.append(k[1:], 0.0)
+    marking = a < n_nets
+    init = 28.0 * n + 12.0 * float(k[0] if len(k) else 0.0) + 4.0 * n_nets
+    asg = 16.0 * w + (4.0 + 8.0 * windows) * k + 8.0 * k * marking
+    det = 8.0 * a + 4.0 * n_nets * marking + 16.0 * m + 4.0 * wn
+    com = 8.0 * w + 16.0 * (w - wn) + 12.0 * (k - kn) + 4.0 * wn
+    # the method's bytes for detection as the paper states it (nets with a
+    # worklist member, 8 per net + 12 per member + the next worklist), for
+    # context; round 1 is one pass over every net
+    meth = 8.0 * a + 12.0 * m + 4.0 * wn
+    if len(meth):
+        meth[0] = 8.0 * n_nets + 12.0 * members_total + 4.0 * wn[0]
+    return {"net_init": init, "net_assign": float(asg.sum()), "net_detect": float(det.sum()),
+            "net_commit": float(com.sum()), "method_detect": float(meth.sum())}
+
+
 # --------------------------------------------------------------------------
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -229,16 +312,131 @@ def load_peaks():
 
 
 def cpu_info():
+    """Architecture, CPU model and core count of this host (the model from
+    /proc/cpuinfo's model name, else lscpu's, else the Arm implementer/part
+    codes)."""
+    import platform
     model = None
+    fields = {}
     try:
         for l in open("/proc/cpuinfo"):
-            if l.lower().startswith(("model name", "cpu model")):
-                model = l.split(":", 1)[1].strip()
-                break
+            if ":" in l:
+                k, v = l.split(":", 1)
+                fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
-    import platform
+    model = fields.get("model name") or fields.get("cpu model")
+    if not model:
+        try:
+            r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+            for l in r.stdout.splitlines():
+                if l.lower().startswith("model name:"):
+                    model = l.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if not model and "cpu part" in fields:
+        model = f"implementer {fields.get('cpu implementer')} part {fields['cpu part']}"
     return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
+def oracle_job(spec):
+    """One timed oracle coloring in a worker process (the oracle as it
+    stands, one thread).  spec = (kind, params...).  Returns (seconds,
+    units, rounds, num_colors) with units = edges (D1/D2: nnz / 2) or
+    entries (PD2: nnz); the input is generated before the clock starts."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2107_00075_gb300 import inputs
+    kind = spec[0]
+    if kind == "rmat_d1":
+        g = inputs.rmat(spec[1], spec[2], seed=SEED, **RMAT)
+        t0 = time.perf_counter()
+        r = oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+        return time.perf_counter() - t0, g.nnz / 2, r.rounds, r.num_colors
+    if kind == "stencil_d1":
+        g = inputs.stencil3d(spec[1], spec[1], spec[1], points=spec[2])
+        reps = spec[3]
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+        return (time.perf_counter() - t0) / reps, g.nnz / 2, r.rounds, r.num_colors
+    if kind == "stencil_d2":
+        g = inputs.stencil3d(spec[1], spec[1], spec[1], points=27)
+        t0 = time.perf_counter()
+        r = oracle.color_d2(g.row_ptr, g.col_idx, seed=SEED)
+        return time.perf_counter() - t0, g.nnz / 2, r.rounds, r.num_colors
+    if kind == "bip_pd2":
+        b = inputs.bipartite(spec[1], spec[2], seed=SEED)
+        t0 = time.perf_counter()
+        r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                             seed=SEED)
+        return time.perf_counter() - t0, float(b.nnz), r.rounds, r.num_colors
+    if kind == "batch_members":
+        sizes, degs = inputs.batch_plan(spec[1])
+        secs = units = 0.0
+        rounds = ncol = 0
+        for i in spec[2]:
+            g = inputs.batch_member(i, sizes, degs)
+            t0 = time.perf_counter()
+            r = oracle.color_d1(g.row_ptr, g.col_idx, seed=SEED)
+            secs += time.perf_counter() - t0
+            units += g.nnz / 2
+            rounds, ncol = max(rounds, r.rounds), max(ncol, r.num_colors)
+        return secs, units, rounds, ncol
+    if kind == "serve_requests":
+        secs = units = 0.0
+        rounds = ncol = 0
+        for req in spec[1]:
+            (k, n, payload_seed), sd = req
+            if k == "d1":
+                g = inputs.rmat(int(np.ceil(np.log2(n))), 8, seed=payload_seed, n_vertices=n)
+                t0 = time.perf_counter()
+                r = oracle.color_d1(g.row_ptr, g.col_idx, seed=sd)
+                u = g.nnz / 2
+            else:
+                b = inputs.bipartite(max(1, int(0.8 * n)), max(1, int(0.2 * n)),
+                                     seed=payload_seed)
+                t0 = time.perf_counter()
+                r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr,
+                                     b.row_idx, seed=sd)
+                u = float(b.nnz)
+            secs += time.perf_counter() - t0
+            units += u
+            rounds, ncol = max(rounds, r.rounds), max(ncol, r.num_colors)
+        return secs, units, rounds, ncol
+    raise ValueError(kind)
+
+
+class CpuPool:
+    """Oracle jobs in spawned worker processes (spawn: safe after CUDA is
+    initialised in this process), one thread each."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.workers = workers
+        self.ex = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+    def submit(self, spec):
+        return self.ex.submit(oracle_job, spec)
+
+    def close(self):
+        self.ex.shutdown(wait=True, cancel_futures=True)
+
+
+def baseline_entry(res, unit, sample, cores=1, extra=None):
+    """cpu_baseline object from oracle_job results [(secs, units, rounds,
+    ncol), ...] run on `cores` worker processes in parallel: rate = total
+    units / (total seconds / cores)."""
+    secs = sum(r[0] for r in res)
+    units = sum(r[1] for r in res)
+    wall = secs / max(1, cores)
+    out = {"value": units / wall if wall > 0 else None, "unit": unit, "cores": cores,
+           "kind": "oracle", "sample": sample, "cpu_seconds": round(secs, 2), **cpu_info()}
+    if extra:
+        out.update(extra)
+    return out
 
 
 def oracle_edges_per_s(scale: int, repeats: int = 1):
@@ -343,7 +541,7 @@ def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> flo
     return world * units_per_rank / (ms_per_step / 1000.0)
 
 
-def bench_batch(pgc, inputs, torch, dev, num_graphs):
+def bench_batch(pgc, inputs, torch, dev, num_graphs, peak=None, peak_kind="measured"):
     """The batched form vs one plain pgc_color_d1 call per graph, inputs
     resident on the device, identical colorings checked."""
     t0 = time.time()
@@ -388,158 +586,374 @@ def bench_batch(pgc, inputs, torch, dev, num_graphs):
     plain_ms = ev0.elapsed_time(ev1)
     same = all(torch.equal(colors[int(b.vtx_off[g]):int(b.vtx_off[g + 1])], per[g][2])
                for g in range(num_graphs))
-    return {"workload": f"{num_graphs} graphs: 2D 5-point grids and G(n,m) with avg degree "
-                        "U[2,32], n log-uniform [100, 200000]",
-            "graphs": num_graphs, "vertices": N, "entries": E, "edges": E // 2,
-            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
-            "batched_edges_per_s": (E / 2) / (batched_ms / 1000),
-            "plain_edges_per_s": (E / 2) / (plain_ms / 1000), "identical_colors": bool(same),
-            "max_rounds": int(gr.max().item()), "gen_s": gen_s, "autotuned": True}
+    out = {"workload": f"{num_graphs} graphs: 2D 5-point grids and G(n,m) with avg degree "
+                       "U[2,32], n log-uniform [100, 200000]",
+           "graphs": num_graphs, "vertices": N, "entries": E, "edges": E // 2,
+           "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+           "batched_edges_per_s": (E / 2) / (batched_ms / 1000),
+           "plain_edges_per_s": (E / 2) / (plain_ms / 1000), "identical_colors": bool(same),
+           "max_rounds": int(gr.max().item()), "gen_s": gen_s, "autotuned": True}
+    del per
+    if peak is not None:
+        # one more call in host-loop mode with the tuned configuration: per-kernel
+        # CUDA-event times and the per-round trace of the whole batch
+        prof = pgc.Profile(trace_cap=1 << 12)
+        pgc.pgc_color_d1_batch(vo, no, rp, ci, seed=SEED, colors=colors, rounds_per_graph=gr,
+                               colors_per_graph=gc, flags=pgc.PGC_AUTOTUNE | pgc.PGC_HOST_LOOP,
+                               profile=prof, stream=stream)
+        G = num_graphs
+        d = np.diff(b.row_ptr.astype(np.int64))
+        deg = np.delete(d, b.vtx_off[1:-1] + np.arange(G - 1))
+        tw = prof.trace_w
+        tail_at = next((i for i in range(1, len(tw)) if 0 < tw[i] <= 4096), None)
+        nb = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, N, E, tail_at, deg)
+        top = max(prof.kernel_ms, key=prof.kernel_ms.get)
+        out["roofline"] = roofline_entry(top, prof.kernel_ms[top], prof.kernel_launches[top],
+                                         nb[top], peak, peak_kind, "d1_engine.cuh")
+        out["kernels"] = kernel_table(prof, nb)
+        step_bytes = float(sum(nb.values()))
+        out["roofline"]["step_bytes"] = step_bytes
+        out["roofline"]["step_frac"] = step_bytes / (batched_ms / 1000.0) / 1e9 / peak
+    return out
 
 
-def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, slots, seed=7):
-    """Served form vs a plain FIFO of single calls, same Poisson arrivals.
-    Payloads (70% D1 R-MAT scale-matched, edge factor 8; 30% PD2 rows
-    0.8n x columns 0.2n, rows 1 + Poisson(7); n log-uniform [1K, 4M]) are
-    generated ahead into pinned host memory; every request has its own seed.
-    Latency = completion - arrival, host-to-device upload included."""
-    import threading
+def serve_plan(n_requests, n_payloads, seed=7):
+    """Request stream of the served workload: payload i (kind, n, payload
+    seed) with n log-uniform on [1K, 4M], 70% D1 (R-MAT scale-matched, edge
+    factor 8) and 30% PD2 (0.8n rows x 0.2n columns, rows 1 + Poisson(7));
+    request j uses payload j mod n_payloads with its own coloring seed."""
     rng = np.random.default_rng(seed)
     payloads = []
     for i in range(n_payloads):
         n = int(np.exp(rng.uniform(np.log(1000), np.log(4_000_000))))
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        if rng.random() < 0.7:
-            g = inputs.rmat(int(np.ceil(np.log2(n))), 8, seed=1000 + i, n_vertices=n)
-            payloads.append(("d1", n, (pin(g.row_ptr), pin(g.col_idx)), g.nnz // 2))
-        else:
-            bp = inputs.bipartite(max(1, int(0.8 * n)), max(1, int(0.2 * n)), seed=2000 + i)
-            payloads.append(("pd2", bp.n_cols, (bp.n_rows, bp.n_cols, pin(bp.row_ptr),
-                                               pin(bp.col_idx), pin(bp.col_ptr), pin(bp.row_idx)),
-                             bp.nnz))
-    reqs = [(payloads[i % n_payloads], int(rng.integers(1, 1 << 40))) for i in range(n_requests)]
-    pinned = lambda k: torch.zeros(k, dtype=torch.int32).pin_memory().numpy()
-    outs_plain = [pinned(p[1]) for p, _ in reqs]
-    outs_srv = [pinned(p[1]) for p, _ in reqs]
+        kind = "d1" if rng.random() < 0.7 else "pd2"
+        payloads.append((kind, n, (1000 if kind == "d1" else 2000) + i))
+    seeds = [int(x) for x in rng.integers(1, 1 << 40, size=n_requests)]
+    return payloads, [(payloads[j % n_payloads], seeds[j]) for j in range(n_requests)]
 
-    def plain_call(i):
-        (kind, n, a, _), sd = reqs[i]
+
+class _Digest:
+    """Order-sensitive 64-bit digest of a color array (a weighted sum with
+    fixed pseudo-random odd weights), so that outputs can be compared across
+    runs without keeping them."""
+
+    def __init__(self, n_max):
+        rng = np.random.default_rng(12345)
+        self.w = rng.integers(1, 1 << 62, size=n_max, dtype=np.int64) | 1
+
+    def __call__(self, a):
+        a = np.asarray(a)
+        return int(np.dot(a.astype(np.int64), self.w[:len(a)]) & ((1 << 63) - 1))
+
+
+def bench_serve(pgc, inputs, torch, n_requests, n_payloads, load, slots, sweep_loads=(),
+                sweep_requests=0, seed=7, budget=48 << 30):
+    """Served form vs a live single-worker FIFO of plain calls under the same
+    Poisson arrivals, at load `load` of the plain path's measured capacity
+    (n_requests requests), plus sweep_loads with sweep_requests each and one
+    saturated run per arm (everything submitted at once) for capacity.
+    Latency = completion - arrival, host-to-device upload included; both arms
+    take pinned host payloads and write pinned host colors; every run's
+    per-request color digests must agree with the plain arm's."""
+    import queue
+    import threading
+    t_gen = time.time()
+    payloads, reqs = serve_plan(max(n_requests, sweep_requests), n_payloads, seed)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    data, units, n_out = [], [], []
+    for kind, n, ps in payloads:
         if kind == "d1":
-            pgc.pgc_color_d1(a[0], a[1], seed=sd, colors=outs_plain[i])
+            g = inputs.rmat(int(np.ceil(np.log2(n))), 8, seed=ps, n_vertices=n)
+            data.append((pin(g.row_ptr), pin(g.col_idx)))
+            units.append(g.nnz // 2)
+            n_out.append(n)
         else:
-            pgc.pgc_color_pd2(*a, seed=sd, colors=outs_plain[i])
+            b = inputs.bipartite(max(1, int(0.8 * n)), max(1, int(0.2 * n)), seed=ps)
+            data.append((b.n_rows, b.n_cols, pin(b.row_ptr), pin(b.col_idx), pin(b.col_ptr),
+                         pin(b.row_idx)))
+            units.append(b.nnz)
+            n_out.append(b.n_cols)
+    gen_s = time.time() - t_gen
+    P = n_payloads
+    digest = _Digest(max(n_out))
+    outs = [torch.zeros(k, dtype=torch.int32).pin_memory().numpy() for k in n_out]
 
-    for i in range(min(4, n_requests)):     # warm-up
-        plain_call(i)
-    # plain service time per request (FIFO capacity)
-    svc = []
-    for i in range(n_requests):
-        t0 = time.perf_counter()
-        plain_call(i)
-        svc.append(time.perf_counter() - t0)
-    cap = n_requests / sum(svc)
-    rate = load * cap
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
-    # FIFO of plain calls under the same arrivals (single worker)
-    t_free, lat_plain = 0.0, []
-    for a, sv in zip(arrivals, svc):
-        start = max(a, t_free)
-        t_free = start + sv
-        lat_plain.append(t_free - a)
-    # served: a producer submits at the arrival times, the caller waits
-    budget = 48 << 30
-    lat_srv = [0.0] * n_requests
-    with pgc.PgcServer(hbm_budget_bytes=budget, max_active=slots) as srv:
-        # warm every slot (graph instantiation, pinned staging) before timing
-        warm = [(i % n_requests) for i in range(2 * slots)]
-        wids = []
-        for i in warm:
-            (kind, n, a, _), sd = reqs[i]
-            wids.append(srv.submit_d1(a[0], a[1], seed=sd) if kind == "d1"
-                        else srv.submit_pd2(*a, seed=sd))
-        for rid in wids:
-            srv.wait(rid)
-        ids = [None] * n_requests
+    def plain_call(j):
+        p = j % P
+        sd = reqs[j][1]
+        if payloads[p][0] == "d1":
+            pgc.pgc_color_d1(data[p][0], data[p][1], seed=sd, colors=outs[p])
+        else:
+            pgc.pgc_color_pd2(*data[p], seed=sd, colors=outs[p])
+        return digest(outs[p])
+
+    def run_plain(count, arrivals):
+        """FIFO: a producer enqueues request j at arrivals[j] (None: all at
+        once); one worker thread serves the queue in order."""
+        q = queue.Queue()
+        lat, dig = [0.0] * count, [0] * count
         t_start = time.perf_counter()
-        t_sub = [0.0] * n_requests
 
-        def producer():
-            for i in range(n_requests):
-                delay = t_start + arrivals[i] - time.perf_counter()
+        def worker():
+            for _ in range(count):
+                j, t_arr = q.get()
+                dig[j] = plain_call(j)
+                lat[j] = time.perf_counter() - t_arr
+        th = threading.Thread(target=worker)
+        th.start()
+        for j in range(count):
+            if arrivals is not None:
+                delay = t_start + arrivals[j] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-                (kind, n, a, _), sd = reqs[i]
-                t_sub[i] = time.perf_counter()
-                ids[i] = (srv.submit_d1(a[0], a[1], seed=sd, colors=outs_srv[i]) if kind == "d1"
-                          else srv.submit_pd2(*a, seed=sd, colors=outs_srv[i]))
+                q.put((j, t_start + arrivals[j]))
+            else:
+                q.put((j, t_start))
+        th.join()
+        return lat, dig, time.perf_counter() - t_start
 
+    def run_served(srv, count, arrivals):
+        """A producer submits request j at arrivals[j] (None: at once; it
+        holds back while P requests are outstanding, since request j writes
+        payload j mod P's output buffer); this thread waits in order."""
+        ids = [None] * count
+        lat, dig = [0.0] * count, [0] * count
+        done = threading.Semaphore(P)
+        t_start = time.perf_counter()
+
+        def producer():
+            for j in range(count):
+                if arrivals is not None:
+                    delay = t_start + arrivals[j] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                done.acquire()
+                p = j % P
+                sd = reqs[j][1]
+                ids[j] = (srv.submit_d1(data[p][0], data[p][1], seed=sd, colors=outs[p])
+                          if payloads[p][0] == "d1" else
+                          srv.submit_pd2(*data[p], seed=sd, colors=outs[p]))
         th = threading.Thread(target=producer)
         th.start()
-        th.join()
-        for i in range(n_requests):
-            _, info = srv.wait(ids[i])
+        for j in range(count):
+            while ids[j] is None:
+                time.sleep(0.0002)
+            _, info = srv.wait(ids[j])
+            t_arr = t_start + (arrivals[j] if arrivals is not None else 0.0)
             # steady-clock stamps share time.perf_counter's clock (CLOCK_MONOTONIC)
-            lat_srv[i] = info.t_done_ns * 1e-9 - (t_start + arrivals[i])
-        wall = time.perf_counter() - t_start
+            lat[j] = info.t_done_ns * 1e-9 - t_arr
+            dig[j] = digest(outs[j % P])
+            done.release()
+        th.join()
+        return lat, dig, time.perf_counter() - t_start
+
+    q = lambda v, x: float(np.percentile(v, x) * 1000) if len(v) else None
+    rng = np.random.default_rng(seed + 1)
+    for j in range(min(8, len(reqs))):           # warm the plain path
+        plain_call(j)
+    n_sat = max(sweep_requests, min(n_requests, 2000))
+    lat_p, dig_ref, wall_p = run_plain(n_sat, None)
+    cap = n_sat / wall_p
+    edges = lambda count: float(sum(units[j % P] for j in range(count)))
+    out = {"workload": f"Poisson arrivals; requests cycle over {P} payloads generated ahead "
+                       "into pinned host memory (70% D1 R-MAT edge factor 8, 30% PD2 0.8n x "
+                       "0.2n rows 1 + Poisson(7), n log-uniform [1K, 4M]), each request its "
+                       "own seed", "payload_gen_s": round(gen_s, 1), "slots": slots,
+           "budget_bytes": budget, "plain_capacity_per_s": cap,
+           "saturated": {"requests": n_sat, "plain_req_per_s": cap,
+                         "plain_edges_per_s": edges(n_sat) / wall_p}}
+    identical = True
+    runs = []
+    with pgc.PgcServer(hbm_budget_bytes=budget, max_active=slots) as srv:
+        for j in range(min(2 * slots, len(reqs))):   # warm every slot
+            p = j % P
+            rid = (srv.submit_d1(data[p][0], data[p][1], seed=reqs[j][1]) if payloads[p][0] == "d1"
+                   else srv.submit_pd2(*data[p], seed=reqs[j][1]))
+            srv.wait(rid)
+        lat_s, dig_s, wall_s = run_served(srv, n_sat, None)
+        identical &= dig_s == dig_ref[:n_sat]
+        out["saturated"].update({"served_req_per_s": n_sat / wall_s,
+                                 "served_edges_per_s": edges(n_sat) / wall_s,
+                                 "speedup": wall_p / wall_s})
+        for rho, count in [(load, n_requests)] + [(x, sweep_requests) for x in sweep_loads]:
+            if count <= 0:
+                continue
+            arrivals = np.cumsum(rng.exponential(1.0 / (rho * cap), count))
+            lat_s, dig_s, wall_s = run_served(srv, count, arrivals)
+            lat_p, dig_p, wall_p2 = run_plain(count, arrivals)
+            same = dig_s == dig_p and dig_p[:min(count, n_sat)] == dig_ref[:min(count, n_sat)]
+            identical &= same
+            runs.append({"load": rho, "requests": count, "rate_per_s": rho * cap,
+                         "p50_ms": q(lat_s, 50), "p99_ms": q(lat_s, 99),
+                         "plain_fifo_p50_ms": q(lat_p, 50), "plain_fifo_p99_ms": q(lat_p, 99),
+                         "served_wall_s": wall_s, "plain_wall_s": wall_p2,
+                         "served_edges_per_s": edges(count) / wall_s,
+                         "identical_colors": bool(same)})
+            log("[serve]", json.dumps(runs[-1]))
         st = srv.stats()
-    same = all(np.array_equal(a, b) for a, b in zip(outs_plain, outs_srv))
-    edges = sum(p[3] for p, _ in reqs)
-    q = lambda v, x: float(np.percentile(v, x) * 1000)
-    return {"workload": f"{n_requests} requests over {n_payloads} payloads, 70% D1 / 30% PD2, "
-                        "n log-uniform [1K, 4M], Poisson arrivals",
-            "load": load, "rate_per_s": rate, "plain_capacity_per_s": cap,
-            "p50_ms": q(lat_srv, 50), "p99_ms": q(lat_srv, 99),
-            "plain_fifo_p50_ms": q(lat_plain, 50), "plain_fifo_p99_ms": q(lat_plain, 99),
-            "served_edges_per_s": edges / wall, "plain_edges_per_s": edges / sum(svc),
-            "slots": slots,
-            "max_active_seen": st["max_active_seen"], "peak_bytes": st["peak_bytes"],
-            "budget_bytes": budget, "identical_colors": bool(same)}
+    head = runs[0] if runs else {}
+    out.update({"load": load, "requests": n_requests, "p50_ms": head.get("p50_ms"),
+                "p99_ms": head.get("p99_ms"), "plain_fifo_p50_ms": head.get("plain_fifo_p50_ms"),
+                "plain_fifo_p99_ms": head.get("plain_fifo_p99_ms"), "runs": runs,
+                "max_active_seen": st["max_active_seen"], "peak_bytes": st["peak_bytes"],
+                "identical_colors": bool(identical),
+                "input_bytes": float(sum(sum(x.nbytes for x in d if hasattr(x, "nbytes"))
+                                         for d in data)),
+                "output_bytes": float(sum(o.nbytes for o in outs))})
+    # lower-bound roofline of the saturated served run: each request's inputs
+    # and colors must cross HBM at least once
+    per_req = [(sum(x.nbytes for x in data[j % P] if hasattr(x, "nbytes")) +
+                outs[j % P].nbytes) for j in range(n_sat)]
+    wall_sat = n_sat / out["saturated"]["served_req_per_s"]
+    out["min_bytes_per_s"] = float(sum(per_req)) / wall_sat
+    out["plan"] = (payloads, [r[1] for r in reqs[:n_sat]])
+    return out
 
 
-def bench_net(pgc, inputs, torch, dev, reps=5, warm=2, flags=0, timeout_ms=0):
+def source_sha(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2107_00075_gb300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+def dram_ratio(kernel, source):
+    """DRAM bytes / design bytes of `kernel` from a committed ncu capture on a
+    small case (profiles/dram_traffic.json), or None when the kernel's source
+    file has changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    d = json.load(open(path)).get(kernel)
+    if not d or d.get("kernel_source_sha256") != source_sha(source):
+        return None, None
+    return d["dram_bytes"] / d["design_bytes"], d.get("workload")
+
+
+def roofline_entry(kernel, ms_total, launches, bytes_total, peak, peak_kind, source):
+    """Roofline of one kernel: design bytes per launch over its average
+    CUDA-event launch time, against the measured HBM copy peak; traffic and
+    dram_frac from the committed small-case ncu capture scaled by the design
+    bytes (units processed), when the source is unchanged."""
+    avg_s = ms_total / 1000.0 / max(1, launches)
+    per = bytes_total / max(1, launches)
+    achieved = per / avg_s / 1e9 if avg_s > 0 else None
+    ratio, cap = dram_ratio(kernel, source)
+    traffic = ratio * per if ratio is not None else None
+    out = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak if achieved else None, "traffic": traffic,
+           "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+           "alg_bytes_per_launch": per, "avg_launch_ms": avg_s * 1000.0, "launches": launches,
+           "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic is not None else None,
+           "dram_capture": cap}
+    return out
+
+
+def kernel_table(prof, nbytes):
+    return {name: {"ms": kms, "launches": prof.kernel_launches[name],
+                   "alg_bytes": nbytes.get(name)} for name, kms in prof.kernel_ms.items()}
+
+
+def bench_net(pgc, inputs, torch, dev, reps=5, warm=2, flags=0, timeout_ms=0, peak=None,
+              peak_kind="measured", profile=True):
     """Distance-2 on the 27-point stencil 128^3 and partial distance-2 on the
     4M x 1M pattern, inputs resident; edges = nnz/2 for D2 (a symmetric
-    graph) and nnz for PD2 (row-column entries)."""
+    graph) and nnz for PD2 (row-column entries).  With profile=True, one more
+    call in host-loop mode gives per-kernel CUDA-event times, the per-round
+    trace, design bytes per kernel and the roofline of the dominant kernel."""
     out = {}
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(call):
+        for _ in range(warm):
+            r = call(0, None)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(reps):
+            r = call(flags, None)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        return r, ev0.elapsed_time(ev1) / reps
+
+    def profiled(call, name, n, n_nets, members_total, units, ms):
+        prof = pgc.Profile(trace_cap=1 << 14)
+        call(pgc.PGC_HOST_LOOP, prof)
+        nb = net_algorithmic_bytes(prof.trace_w, prof.trace_h, prof.trace_nets,
+                                   prof.trace_members, n, n_nets, members_total)
+        top = max(prof.kernel_ms, key=prof.kernel_ms.get)
+        rf = roofline_entry(top, prof.kernel_ms[top], prof.kernel_launches[top], nb[top], peak,
+                            peak_kind, "net.cu")
+        if top == "net_detect":
+            rf["method_bytes_per_launch"] = nb["method_detect"] / prof.kernel_launches[top]
+        step_bytes = sum(v for k, v in nb.items() if k.startswith("net_"))
+        return {"roofline": rf, "kernels": kernel_table(prof, nb),
+                "step_bytes": step_bytes,
+                "step_frac": step_bytes / (ms / 1000.0) / 1e9 / peak,
+                "nets_per_round": prof.trace_nets.tolist()[:4]}
+
     g = inputs.stencil3d(128, 128, 128, points=27)
     rp, ci = t(g.row_ptr), t(g.col_idx)
     col = torch.empty(g.n, dtype=torch.int32, device=dev)
-    for _ in range(warm):
-        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream, flags=flags,
-                             timeout_ms=timeout_ms)
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    for _ in range(reps):
-        r = pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream, flags=flags,
-                             timeout_ms=timeout_ms)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / reps
-    out["d2_stencil27_128"] = {"n": g.n, "nnz": g.nnz, "ms": ms, "rounds": r.rounds,
-                               "num_colors": r.num_colors,
-                               "edges_per_s": (g.nnz / 2) / (ms / 1000)}
+    d2 = lambda fl, prof: pgc.pgc_color_d2(rp, ci, seed=SEED, colors=col, stream=stream,
+                                           flags=fl, timeout_ms=timeout_ms, profile=prof)
+    r, ms = timed(d2)
+    e = {"workload": "D2, 27-point stencil 128^3", "n": g.n, "nnz": g.nnz, "ms": ms,
+         "rounds": r.rounds, "num_colors": r.num_colors, "edges_per_s": (g.nnz / 2) / (ms / 1000)}
+    if profile:
+        e.update(profiled(d2, "d2", g.n, g.n, g.nnz + g.n, g.nnz / 2, ms))
+    out["d2_stencil27_128"] = e
     del rp, ci, col
     b = inputs.bipartite(1 << 22, 1 << 20, seed=SEED)
     a = [t(x) for x in (b.row_ptr, b.col_idx, b.col_ptr, b.row_idx)]
     col = torch.empty(b.n_cols, dtype=torch.int32, device=dev)
-    for _ in range(warm):
-        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream,
-                              flags=flags, timeout_ms=timeout_ms)
+    pd2 = lambda fl, prof: pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col,
+                                             stream=stream, flags=fl, timeout_ms=timeout_ms,
+                                             profile=prof)
+    r, ms = timed(pd2)
+    e = {"workload": "PD2, 4,194,304 x 1,048,576 pattern, rows 1 + Poisson(7)",
+         "rows": b.n_rows, "cols": b.n_cols, "nnz": b.nnz, "ms": ms, "rounds": r.rounds,
+         "num_colors": r.num_colors, "edges_per_s": b.nnz / (ms / 1000)}
+    if profile:
+        e.update(profiled(pd2, "pd2", b.n_cols, b.n_rows, b.nnz, b.nnz, ms))
+    out["pd2_4Mx1M"] = e
+    return out
+
+
+def recorded_full_size_oracle():
+    """The oracle's wall time on the full workloads as recorded by the
+    full-size parity tests on the GB300 host (profiles/oracle_full_size.json,
+    written by tests/test_gpu_full_size.py), or {}."""
+    path = os.path.join(ROOT, "profiles", "oracle_full_size.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def bench_small_d1(pgc, inputs, torch, dev, reps=200):
+    """D1 on the 7-point stencil 32^3 (32,768 vertices, 190,464 entries):
+    CUDA-event time of `reps` back-to-back calls, inputs resident."""
+    g = inputs.stencil3d(32, 32, 32, points=7)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    col = torch.empty(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(5):
+        r = pgc.pgc_color_d1(rp, ci, seed=SEED, colors=col, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     for _ in range(reps):
-        r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, *a, seed=SEED, colors=col, stream=stream,
-                              flags=flags, timeout_ms=timeout_ms)
+        r = pgc.pgc_color_d1(rp, ci, seed=SEED, colors=col, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1) / reps
-    out["pd2_4Mx1M"] = {"rows": b.n_rows, "cols": b.n_cols, "nnz": b.nnz, "ms": ms,
-                        "rounds": r.rounds, "num_colors": r.num_colors,
-                        "edges_per_s": b.nnz / (ms / 1000)}
-    return out
+    prof = pgc.Profile(trace_cap=1 << 12)
+    pgc.pgc_color_d1(rp, ci, seed=SEED, colors=col, stream=stream, flags=pgc.PGC_HOST_LOOP,
+                     profile=prof)
+    return g, {"workload": "D1, 7-point stencil 32^3", "n": g.n, "nnz": g.nnz, "ms": ms,
+               "rounds": r.rounds, "num_colors": r.num_colors,
+               "edges_per_s": (g.nnz / 2) / (ms / 1000.0), "reps": reps,
+               "note": "each call synchronizes its stream (rounds and colors are returned "
+                       "by value), so this is per-call latency, not a bandwidth figure"}, prof
 
 
 def main():
@@ -556,9 +970,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--serve-payloads", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-payloads", type=int, default=128)
     ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-sweep", default="0.5,0.9",
+                    help="further loads of the served comparison (comma separated)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=2500)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--loop", default="device", choices=["device", "host"],
                     help="round loop of the timed steps: device-side CUDA graph (default) or "
@@ -569,6 +986,7 @@ def main():
                          "cooperative launch on the subgraph the worklist induces (0: library default, < 0: never)")
     ap.add_argument("--timeout-ms", type=int, default=0,
                     help="device round-loop budget (raise it for runs under a profiler)")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -597,6 +1015,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    peak, peak_kind = load_peaks()
 
     def barrier():
         if world > 1:
@@ -607,7 +1026,8 @@ def main():
             flags = pgc.PGC_HOST_LOOP if args.loop == "host" else 0
             print(json.dumps(bench_net(pgc, inputs, torch, dev, reps=args.steps,
                                        warm=args.warmup, flags=flags,
-                                       timeout_ms=args.timeout_ms)), flush=True)
+                                       timeout_ms=args.timeout_ms, peak=peak,
+                                       peak_kind=peak_kind, profile=False)), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -682,12 +1102,32 @@ def main():
                "d2h_bytes_per_step": int(4 * n), "ms_per_step": 1000 * dt,
                "stat": f"median of {e_steps} calls", "mean_ms": 1000 * float(np.mean(calls)),
                "calls_ms": [round(1000 * c, 2) for c in calls]}
+        del h_rp, h_ci, h_col
+
+    # ---- CPU legs: the oracle on bounded samples, in spawned workers that
+    #      run while the device-timed legs below proceed ----
+    pool = None
+    futs = {}
+    serve_plan_args = (max(args.serve_requests, args.serve_sweep_requests), args.serve_payloads)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = CpuPool(max(1, min(8, (os.cpu_count() or 4) - 4)))
+        futs["rmat"] = [pool.submit(("rmat_d1", args.cpu_baseline_scale, args.edge_factor))]
+        futs["small"] = [pool.submit(("stencil_d1", 32, 7, 20))]
+        futs["d2"] = [pool.submit(("stencil_d2", 64))]
+        futs["pd2"] = [pool.submit(("bip_pd2", 1 << 20, 1 << 18))]
+        members = list(range(0, args.batch_graphs, 8))
+        futs["batch"] = [pool.submit(("batch_members", args.batch_graphs, members[k::4]))
+                         for k in range(4)]
+        pay, rq = serve_plan(*serve_plan_args)
+        sample = rq[:96]
+        futs["serve"] = [pool.submit(("serve_requests", sample[k::4])) for k in range(4)]
 
     # ---- roofline of the dominant kernel (host-loop mode, CUDA events) ----
     roofline = None
     kernels = {}
     trace_w = None
-    peak, peak_kind = load_peaks()
+    step_bytes = None
+    deg = np.diff(g.row_ptr)
     if not args.no_profile:
         prof = pgc.Profile(trace_cap=1 << 16, launch_cap=1 << 18)
         pgc.pgc_color_d1(rp, ci, seed=SEED, colors=colors, stream=stream,
@@ -703,58 +1143,61 @@ def main():
         if tail_w > 0:
             tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
         nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, n, nnz,
-                                      tail_at)
-        for name, kms in prof.kernel_ms.items():
-            kernels[name] = {"ms": kms, "launches": prof.kernel_launches[name],
-                             "alg_bytes": nbytes.get(name)}
+                                      tail_at, deg)
+        kernels = kernel_table(prof, nbytes)
         top = max(prof.kernel_ms, key=prof.kernel_ms.get)
         launches = prof.kernel_launches[top]
-        avg_s = prof.kernel_ms[top] / 1000.0 / launches
-        # bytes this design must move (priority lists, pushed forbidden
-        # sets); the method's own per-round adjacency scan is reported beside
-        # it for context -- this design does not move those bytes
-        per_launch = nbytes[top] / launches
-        method_per_launch = None
+        roofline = roofline_entry(top, prof.kernel_ms[top], launches, nbytes[top], peak,
+                                  peak_kind, "d1_engine.cuh")
+        # the method's own per-round adjacency scan, for context: this design
+        # does not move those bytes (it scans priority lists and stops early)
         if top == "d1_detect":
             tot, _ = d1_method_bytes(prof.trace_w, prof.trace_s, n, nnz, tail_at)
-            method_per_launch = tot / launches
-        achieved = per_launch / avg_s / 1e9
-        # DRAM bytes per launch from an ncu capture (profiles/traffic.json),
-        # used only while the kernel source is the one that was measured
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tpath):
-            import hashlib
-            tr = json.load(open(tpath)).get(top)
-            src = os.path.join(ROOT, "paper_2107_00075_gb300", "csrc", "d1_engine.cuh")
-            cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-            if (tr and tr.get("workload") == f"rmat{args.scale}"
-                    and tr.get("kernel_source_sha256") == cur):
-                traffic = tr.get("bytes_per_launch")
-        roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                    "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
-                    "alg_bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1000,
-                    "launches": launches,
-                    "method_bytes_per_launch": method_per_launch,
-                    "method_rate_gbs": (method_per_launch / avg_s / 1e9
-                                        if method_per_launch else None)}
+            roofline["method_bytes_per_launch"] = tot / launches
+        step_bytes = float(sum(nbytes.values()))
+        roofline["step_bytes"] = step_bytes
+        roofline["step_frac"] = step_bytes / (ms_per_step / 1000.0) / 1e9 / peak
+        roofline["profile_call_ms"] = float(sum(prof.kernel_ms.values()))
 
-    # ---- CPU baseline: the oracle on a bounded sample ----
+    small = net = batch = serve = None
+    if rank == 0 and not args.no_small:
+        sg, small, sprof = bench_small_d1(pgc, inputs, torch, dev)
+        sb = d1_algorithmic_bytes(sprof.trace_w, sprof.trace_s, sprof.trace_h, sg.n, sg.nnz,
+                                  None, np.diff(sg.row_ptr))
+        stop = max(sprof.kernel_ms, key=sprof.kernel_ms.get)
+        small["roofline"] = roofline_entry(stop, sprof.kernel_ms[stop],
+                                           sprof.kernel_launches[stop], sb[stop], peak,
+                                           peak_kind, "d1_engine.cuh")
+        small["kernels"] = kernel_table(sprof, sb)
+        log("[small]", json.dumps({k: v for k, v in small.items() if k != "kernels"}))
+    if rank == 0 and not args.no_net:
+        net = bench_net(pgc, inputs, torch, dev, peak=peak, peak_kind=peak_kind)
+        log("[net]", json.dumps({k: {a: b for a, b in v.items() if a != "kernels"}
+                                 for k, v in net.items()}))
+    if rank == 0 and not args.no_batch:
+        batch = bench_batch(pgc, inputs, torch, dev, args.batch_graphs, peak, peak_kind)
+        log("[batch]", json.dumps({k: v for k, v in batch.items() if k != "kernels"}))
+
+    # ---- collect the CPU legs; the multi-core leg runs alone ----
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        eps, secs, sg, ores = oracle_edges_per_s(args.cpu_baseline_scale)
-        cpu = {"value": eps, "unit": "edges/s", "cores": 1, "kind": "oracle",
-               "sample": f"R-MAT scale {args.cpu_baseline_scale}, edge factor 16 "
-                         f"({sg.nnz} entries, 1/{2**(args.scale-args.cpu_baseline_scale)} of the "
-                         f"workload), one full coloring, {secs:.1f} s", **cpu_info()}
+    full = recorded_full_size_oracle()
+    if pool is not None:
+        got = {k: [f.result() for f in v] for k, v in futs.items()}
+        pool.close()
+        secs, units, ores_rounds, ores_ncol = got["rmat"][0]
+        cpu = baseline_entry(got["rmat"], "edges/s",
+                             f"R-MAT scale {args.cpu_baseline_scale}, edge factor 16 "
+                             f"({int(2 * units)} entries, 1/{2**(args.scale-args.cpu_baseline_scale)}"
+                             f" of the workload), one full coloring, {secs:.1f} s")
+        if "rmat24_d1" in full:
+            cpu["full_workload_recorded"] = full["rmat24_d1"]
         # OpenMP's default wait policy spins at barriers (fast on idle
         # cores, slow if any core is busy); the passive one sleeps: keep the
         # faster of the two
         runs = [x for x in (cpu_parallel_edges_per_s(args.cpu_baseline_scale, timeout=120.0,
                                                      wait_policy="PASSIVE"),
                             cpu_parallel_edges_per_s(args.cpu_baseline_scale, timeout=60.0))
-                if x and (x["rounds"], x["num_colors"]) == (ores.rounds, ores.num_colors)]
+                if x and (x["rounds"], x["num_colors"]) == (ores_rounds, ores_ncol)]
         par = min(runs, key=lambda x: x["secs"]) if runs else None
         if par is not None:
             cpu["parallel"] = {
@@ -764,18 +1207,40 @@ def main():
                 "sample": f"same graph, best of 3 colorings, {par['secs']:.2f} s "
                           f"(OMP_WAIT_POLICY {par['wait_policy']})",
                 "rounds": par["rounds"], "num_colors": par["num_colors"]}
-
-    batch = serve = net = None
-    if rank == 0 and not args.no_net:
-        net = bench_net(pgc, inputs, torch, dev)
-        log("[net]", json.dumps(net))
-    if rank == 0 and not args.no_batch:
-        batch = bench_batch(pgc, inputs, torch, dev, args.batch_graphs)
-        log("[batch]", json.dumps(batch))
+        if small is not None:
+            small["cpu_baseline"] = baseline_entry(
+                got["small"], "edges/s", "the same stencil, 20 colorings (average)")
+        if net is not None:
+            net["d2_stencil27_128"]["cpu_baseline"] = baseline_entry(
+                got["d2"], "edges/s", "D2 on the 27-point stencil 64^3 (1/8 of the vertices)",
+                extra={"full_workload_recorded": full.get("stencil128_d2")})
+            net["pd2_4Mx1M"]["cpu_baseline"] = baseline_entry(
+                got["pd2"], "entries/s",
+                "PD2 on a 1,048,576 x 262,144 pattern of the same recipe (1/4)",
+                extra={"full_workload_recorded": full.get("bip_pd2")})
+        if batch is not None:
+            batch["cpu_baseline"] = baseline_entry(
+                got["batch"], "edges/s", f"every 8th graph of the batch "
+                f"({len(range(0, args.batch_graphs, 8))} graphs), 4 worker processes",
+                cores=4)
+        serve_cpu = baseline_entry(got["serve"], "edges/s",
+                                   "the first 96 requests of the stream, 4 worker processes",
+                                   cores=4)
     if rank == 0 and not args.no_serve:
+        sweep = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
         serve = bench_serve(pgc, inputs, torch, args.serve_requests, args.serve_payloads,
-                            args.serve_load, args.serve_slots)
-        log("[serve]", json.dumps(serve))
+                            args.serve_load, args.serve_slots, sweep, args.serve_sweep_requests)
+        serve.pop("plan", None)
+        mb = serve.pop("min_bytes_per_s")
+        serve["roofline"] = {"bound": "hbm", "kernel": "whole served run (saturated)",
+                             "achieved": mb / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": mb / 1e9 / peak, "traffic": None,
+                             "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+                             "bytes": "one pass over each request's inputs and colors "
+                                      "(a lower bound on what must cross HBM)"}
+        if pool is not None:
+            serve["cpu_baseline"] = serve_cpu
+        log("[serve]", json.dumps({k: v for k, v in serve.items() if k != "runs"}))
 
     if rank == 0:
         # classify, build, tier, then (assign,) detect, push per round until the
@@ -798,7 +1263,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((4 * (n + 1 + nnz)) / 1e9)},
             "nnz_per_s": value * 2, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
-            "batched": batch, "served": serve, "distance2": net,
+            "small_d1": small, "batched": batch, "served": serve, "distance2": net,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -102,6 +102,11 @@ typedef struct {
     float *launch_ms;
     int32_t launch_cap;
     int32_t num_launches;
+    /* D2/PD2 only, nullable host arrays of trace_cap entries: entry r-1
+       describes round r's detection -- the nets it visited (every net, or
+       those with a member on the worklist) and their total member count */
+    int64_t *trace_nets;
+    int64_t *trace_members;
 } pgc_profile;
 
 typedef struct {
@@ -211,15 +216,19 @@ pgc_status pgc_color_d1_batch(int32_t G, const int64_t *vtx_off, const int64_t *
  *   row_ptr, col_idx, colors: DEVICE memory only (host pointers are rejected,
  *           since staging them would need an allocation); layout as
  *           pgc_color_d1.  rounds, num_colors: host outputs.
- *   flags:  PGC_NO_DEGREE_RULE or 0 (other options are fixed to defaults).
+ *   flags:  PGC_NO_DEGREE_RULE or 0.  The other options take pgc_color_d1's
+ *           defaults (the same detection tiers), except that the last rounds
+ *           do not use the core phase: every round runs the per-round kernels,
+ *           which give the same colors.
  *   The first call on a device looks up the array's device address (once per
- *           device, with that device current); make that first call before
- *           any stream capture.
+ *           device and CUDA context, with that device current); make that
+ *           first call before any stream capture.
  *   Every call reuses the same array and the array keeps the previous call's
  *           contents; the call clears what must start at zero.  Two calls
  *           whose GPU work overlapped would race on the array: calls take a
- *           process-wide lock and synchronize `stream` before returning, so
- *           calls made through this function never overlap.
+ *           process-wide lock and synchronize `stream` before returning (on
+ *           error too, once work was enqueued), so calls made through this
+ *           function never overlap.
  */
 pgc_status pgc_color_d1_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                                 uint64_t seed, int32_t *colors, int32_t *rounds,
@@ -305,6 +314,26 @@ pgc_status pgc_release(void);
 
 /* Library version string. */
 const char *pgc_version(void);
+
+/*
+ * Test hooks: fault injection for the failure-path tests (no production use;
+ * the paper has no counterpart).  Both act process-wide on later calls.
+ *
+ * pgc_test_fail_alloc(after): the device allocation the library attempts
+ *   after `after` further successful ones fails as if the device were out of
+ *   memory, once; the call that meets it returns PGC_ERR_OOM having freed
+ *   the scratch of that engine.  after < 0 disarms.
+ * pgc_test_core_barrier(polls, slow_block, slow_us): the grid barrier of the
+ *   D1 core loop gives up after `polls` polls (0: the default, about one
+ *   second), and block `slow_block` of the core loop (-1: none) reaches its
+ *   first barrier `slow_us` microseconds late (at most 2 s, else
+ *   PGC_ERR_INVALID_ARG).  With a late block and a short poll limit the
+ *   waiting blocks give up, and the coloring returns PGC_ERR_TIMEOUT ("a
+ *   grid barrier of the core loop timed out") with the context intact; every
+ *   wait stays bounded.
+ */
+pgc_status pgc_test_fail_alloc(int32_t after);
+pgc_status pgc_test_core_barrier(uint32_t polls, int32_t slow_block, uint32_t slow_us);
 
 #ifdef __cplusplus
 }

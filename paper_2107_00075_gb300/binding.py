@@ -41,7 +41,8 @@ class PgcProfileC(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64 * PGC_MAX_KERNELS),
                 ("kernel_names", ctypes.c_char_p * PGC_MAX_KERNELS),
                 ("launch_slot", ctypes.c_void_p), ("launch_ms", ctypes.c_void_p),
-                ("launch_cap", ctypes.c_int32), ("num_launches", ctypes.c_int32)]
+                ("launch_cap", ctypes.c_int32), ("num_launches", ctypes.c_int32),
+                ("trace_nets", ctypes.c_void_p), ("trace_members", ctypes.c_void_p)]
 
 
 class PgcOptsC(ctypes.Structure):
@@ -78,6 +79,8 @@ class Profile:
     kernel_launches: dict = field(default_factory=dict)
     launch_cap: int = 0          # > 0: record every timed launch (host loop)
     launches: list = field(default_factory=list)   # [(kernel name, ms)]
+    trace_nets: np.ndarray = field(default=None)     # D2/PD2: nets detection visited per round
+    trace_members: np.ndarray = field(default=None)  # D2/PD2: their members per round
 
 
 @dataclass
@@ -132,6 +135,10 @@ def lib():
         L.pgc_version.restype = ctypes.c_char_p
         L.pgc_release.restype = ctypes.c_int
         L.pgc_opts_init.argtypes = [ctypes.POINTER(PgcOptsC)]
+        L.pgc_test_fail_alloc.argtypes = [i32]
+        L.pgc_test_fail_alloc.restype = ctypes.c_int
+        L.pgc_test_core_barrier.argtypes = [ctypes.c_uint32, i32, ctypes.c_uint32]
+        L.pgc_test_core_barrier.restype = ctypes.c_int
         _declared = True
     return L
 
@@ -194,6 +201,10 @@ def _make_opts(flags, max_rounds, mid_degree, hub_degree, block, grid_per_sm, ti
         pc.trace_w = profile.trace_w.ctypes.data
         pc.trace_s = profile.trace_s.ctypes.data
         pc.trace_h = profile.trace_h.ctypes.data
+        profile.trace_nets = np.zeros(profile.trace_cap, dtype=np.int64)
+        profile.trace_members = np.zeros(profile.trace_cap, dtype=np.int64)
+        pc.trace_nets = profile.trace_nets.ctypes.data
+        pc.trace_members = profile.trace_members.ctypes.data
         pc.trace_cap = profile.trace_cap
         if profile.launch_cap > 0:
             profile._slots = np.zeros(profile.launch_cap, dtype=np.int32)
@@ -214,6 +225,8 @@ def _finish_profile(profile: Optional[Profile], keep, rounds):
     profile.trace_w = profile.trace_w[:r].copy()
     profile.trace_s = profile.trace_s[:r].copy()
     profile.trace_h = profile.trace_h[:r].copy()
+    profile.trace_nets = profile.trace_nets[:r].copy()
+    profile.trace_members = profile.trace_members[:r].copy()
     for k in range(pc.num_kernels):
         name = pc.kernel_names[k]
         if name:
@@ -398,6 +411,18 @@ def pgc_color_d1_batch(vtx_off, nnz_off, row_ptr, col_idx, seed: int = 1, colors
     _check(st)
     _finish_profile(profile, keep, rounds.value)
     return BatchResult(colors, rounds_per_graph, colors_per_graph, rounds.value)
+
+
+def pgc_test_fail_alloc(after: int):
+    """Test hook: the device allocation after `after` further successful ones
+    fails once as out of memory (after < 0 disarms); see pgc.h."""
+    _check(lib().pgc_test_fail_alloc(after))
+
+
+def pgc_test_core_barrier(polls: int = 0, slow_block: int = -1, slow_us: int = 0):
+    """Test hook: poll limit of the core loop's grid barrier (0: default) and
+    a late core-loop block (-1: none); see pgc.h."""
+    _check(lib().pgc_test_core_barrier(polls, slow_block, slow_us))
 
 
 def pgc_release():

@@ -1,29 +1,11 @@
 // d1.cu -- pgc_color_d1: distance-1 coloring of one graph (Sec. 3.2-3.3).
 // The engine (kernels and device-side round loop) is in d1_engine.cuh; this
-// file adds argument checks, host-buffer staging and optional validation.
+// file adds argument checks, host-buffer staging and optional validation
+// (validate.cu).
 #include "d1_engine.cuh"
 
 namespace pgc {
 namespace d1 {
-
-// ---------------------------------------------------------------------------
-// optional input validation (PGC_VALIDATE): shape and id range
-// ---------------------------------------------------------------------------
-__global__ void d1_validate_offsets(const int* __restrict__ rp, int n, int* bad) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        if (rp[v + 1] < rp[v]) atomicOr(bad, 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && rp[0] != 0) atomicOr(bad, 1);
-}
-
-// Runs only after the offsets passed, so every e < rp[n] is inside col_idx.
-__global__ void d1_validate_ids(const int* __restrict__ rp, const int* __restrict__ ci, int n,
-                                int* bad) {
-    const long long nnz = rp[n];
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
-        if ((unsigned)ci[e] >= (unsigned)n) atomicOr(bad, 2);
-}
 
 // Staging buffers for host-memory arguments (per device).
 struct Staging {
@@ -119,27 +101,8 @@ static pgc_status color(int32_t n, const int32_t* row_ptr, const int32_t* col_id
         d_col = stg.col.as<int>();
     }
     if (o.flags & PGC_VALIDATE) {
-        if (pgc_status s = stg.flag.ensure(4)) return s;
-        if (pgc_status s = cx->h_state.ensure(sizeof(State))) return s;
-        int* hb = cx->h_state.as<int>();
-        PGC_CUDA(cudaMemsetAsync(stg.flag.ptr, 0, 4, stream));
-        d1_validate_offsets<<<cx->dev.num_sms * 4, 256, 0, stream>>>(d_rp, n, stg.flag.as<int>());
-        PGC_CUDA(cudaGetLastError());
-        PGC_CUDA(cudaMemcpyAsync(hb, stg.flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
-        PGC_CUDA(cudaStreamSynchronize(stream));
-        if (*hb) return fail(PGC_ERR_INVALID_ARG, "row_ptr is not a valid offset array");
-        if (!d_ci) {
-            PGC_CUDA(cudaMemcpyAsync(hb, d_rp + n, 4, cudaMemcpyDeviceToHost, stream));
-            PGC_CUDA(cudaStreamSynchronize(stream));
-            if (*hb != 0) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx with row_ptr[n] > 0");
-        } else {
-            d1_validate_ids<<<cx->dev.num_sms * 4, 256, 0, stream>>>(d_rp, d_ci, n,
-                                                                     stg.flag.as<int>());
-            PGC_CUDA(cudaGetLastError());
-            PGC_CUDA(cudaMemcpyAsync(hb, stg.flag.ptr, 4, cudaMemcpyDeviceToHost, stream));
-            PGC_CUDA(cudaStreamSynchronize(stream));
-            if (*hb) return fail(PGC_ERR_INVALID_ARG, "col_idx entry out of [0, n)");
-        }
+        if (nnz > 0 && !d_ci) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx with row_ptr[n] > 0");
+        if (pgc_status s = validate::symmetric_csr(d_rp, d_ci, n, cx->dev, stream)) return s;
     }
     SingleView view{d_rp, d_ci};
     const Upload up{col_idx, row_ptr, stg.ci.as<int>()};

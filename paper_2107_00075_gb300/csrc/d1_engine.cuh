@@ -184,6 +184,9 @@ struct Problem {
     int det_s;
     int det_m;
     int tail_w;        // hand over to the core phase once the worklist is this small (0: never)
+    unsigned bar_polls;   // core loop: grid-barrier polls before giving up
+    int slow_block;       // test hook: this core-loop block starts late (-1: none)
+    unsigned slow_ns;     // ... by this much
 };
 
 // key(u) > key(v) for u, v of the same graph (hash of graph-local ids),
@@ -580,26 +583,44 @@ __device__ __forceinline__ void queue_push(const Problem<V>& P, int v, int d) {
     for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
 }
 
+// Warp-wide: does any of the H-list entries [b0, min(b0 + 32K, hl)) of v
+// (starting at h) currently hold color t?  K ids per lane are loaded, then
+// their K colors, so a step costs two dependent loads whatever K is.
+template <int K, class V>
+__device__ __forceinline__ bool warp_step(const Problem<V>& P, const int* h, int b0, int hl,
+                                          int t) {
+    const int lane = lane_id();
+    int u[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int e = b0 + 32 * j + lane;
+        u[j] = e < hl ? __ldg(h + e) : -1;
+    }
+    bool hit = false;
+#pragma unroll
+    for (int j = 0; j < K; ++j) hit |= u[j] >= 0 && abs(P.col[u[j]]) == t;
+    return __any_sync(kFullMask, hit);
+}
+
 // Warp-wide: does any of the H-list entries [from, hl) of v (starting at
-// hadj[beg]) currently hold color t?  32 entries per step; the ids of the
-// next step are loaded before this step's colors are compared.
+// hadj[beg]) currently hold color t?  The steps grow 64, 128, 256, 256, ...
+// entries: most losers meet their conflict in the first step, while a
+// winner, which must read its whole list, needs few dependent steps.
 template <class V>
 __device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg, int hl, int t,
                                               int from) {
-    const int lane = lane_id();
     const int* h = P.hadj + beg;
-    for (int b0 = from; b0 < hl; b0 += 32 * 2) {
-        int u[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int e = b0 + 32 * j + lane;
-            u[j] = e < hl ? __ldg(h + e) : -1;
-        }
-        bool hit = false;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) hit |= u[j] >= 0 && abs(P.col[u[j]]) == t;
-        if (__any_sync(kFullMask, hit)) return true;
+    int b0 = from;
+    if (b0 < hl) {
+        if (warp_step<2>(P, h, b0, hl, t)) return true;
+        b0 += 64;
     }
+    if (b0 < hl) {
+        if (warp_step<4>(P, h, b0, hl, t)) return true;
+        b0 += 128;
+    }
+    for (; b0 < hl; b0 += 256)
+        if (warp_step<8>(P, h, b0, hl, t)) return true;
     return false;
 }
 
@@ -726,12 +747,20 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             const long long beg = P.g.begin(g, ent.w);
             t = -col[v];
             lose = first && hl > 0;
-            for (int e = 0; !first && e < hl && !lose; e += 4) {
+            // four list entries, then eight at a time (ids, then their colors)
+            if (!first && hl > 0) {
                 int u[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
+                for (int j = 0; j < 4; ++j) u[j] = j < hl ? __ldg(ha + beg + j) : -1;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) lose |= u[j] >= 0 && abs(col[u[j]]) == t;
+            }
+            for (int e = 4; !first && e < hl && !lose; e += 8) {
+                int u[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) lose |= u[j] >= 0 && abs(col[u[j]]) == t;
             }
             if (lose) {
                 my_s += (unsigned long long)d;
@@ -847,7 +876,7 @@ __global__ void d1_push(const Problem<V>* __restrict__ Pp) {
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  A
 // wait that exceeds ~2^22 polls (about a second) gives up, records the
 // failure and lets the kernel return with an error instead of hanging.
-__device__ __forceinline__ bool grid_barrier(State* st) {
+__device__ __forceinline__ bool grid_barrier(State* st, unsigned max_polls) {
     __threadfence();
     __syncthreads();
     __shared__ int s_ok;
@@ -863,7 +892,7 @@ __device__ __forceinline__ bool grid_barrier(State* st) {
             unsigned polls = 0;
             while (*(volatile unsigned*)&st->bar_gen == gen) {
                 __nanosleep(128);
-                if (++polls > (1u << 22) || *(volatile int*)&st->bar_timeout) {
+                if (++polls > max_polls || *(volatile int*)&st->bar_timeout) {
                     atomicExch(&st->bar_timeout, 1);
                     ok = 0;
                     break;
@@ -901,7 +930,10 @@ __device__ __forceinline__ bool grid_barrier(State* st) {
 // scanned; the induced lists are a subset of W's adjacency, so they fit),
 // per-vertex arrays in the other parity's worklist buffers (3 x 16n bytes).
 
-constexpr int kCoreBlocks = 32;
+#ifndef PGC_CORE_BLOCKS
+#define PGC_CORE_BLOCKS 32
+#endif
+constexpr int kCoreBlocks = PGC_CORE_BLOCKS;
 constexpr int kUploadChunks = 8;    // host adjacency uploaded in this many row ranges
 
 // Adjacency still in (pinned) host memory when a coloring starts: it is
@@ -1200,6 +1232,11 @@ __global__ void __launch_bounds__(1024, 1) d1_core_loop(const Problem<V>* __rest
     const int lane = lane_id(), wpb = blockDim.x >> 5;
     const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    if ((int)blockIdx.x == P.slow_block && threadIdx.x == 0) {
+        // test hook: this block reaches its first barrier late (bounded)
+        const unsigned long long t_end = global_ns() + P.slow_ns;
+        while (global_ns() < t_end) __nanosleep(1000);
+    }
     int side = 0;
     for (;;) {
         const int r = *(volatile int*)&st->round;
@@ -1212,7 +1249,7 @@ __global__ void __launch_bounds__(1024, 1) d1_core_loop(const Problem<V>* __rest
             const int i = lw[x];
             lcol[i] = -first_fit(P, A.lent[i], -lcol[i]);
         }
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, P.bar_polls)) break;
         // detect: one warp per vertex over its higher-priority induced list
         int my_max = 0;
         unsigned long long my_s = 0ull, my_h = 0ull;
@@ -1258,7 +1295,7 @@ __global__ void __launch_bounds__(1024, 1) d1_core_loop(const Problem<V>* __rest
             if (my_s > 0) atomicAdd(&st->s_next, my_s);
             if (my_h > 0) atomicAdd(&st->h_next, my_h);
         }
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, P.bar_polls)) break;
         // push the winners' colors to their uncolored induced neighbors,
         // while one thread closes the round.  The warps share the winners
         // (several warps per winner when winners are few); a warp takes four
@@ -1305,7 +1342,7 @@ __global__ void __launch_bounds__(1024, 1) d1_core_loop(const Problem<V>* __rest
                 }
             }
         }
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, P.bar_polls)) break;
         if (*(volatile int*)&st->done) break;
         side ^= 1;
     }
@@ -1555,6 +1592,17 @@ struct Engine {
     pgc_status run(const V& view, int n, long long nnz, int* d_col, int* g_rounds,
                    int* g_colors, uint64_t seed, const Opts& o, cudaStream_t stream,
                    int* rounds, int* num_colors, const Upload* up = nullptr) {
+        pgc_status s = run_scratch(view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream,
+                                   rounds, num_colors, up);
+        // out of device memory: keep no half-grown scratch (the next call
+        // allocates again)
+        if (s == PGC_ERR_OOM) release();
+        return s;
+    }
+
+    pgc_status run_scratch(const V& view, int n, long long nnz, int* d_col, int* g_rounds,
+                           int* g_colors, uint64_t seed, const Opts& o, cudaStream_t stream,
+                           int* rounds, int* num_colors, const Upload* up) {
         // scratch grows, never shrinks; pointers travel in the Problem struct,
         // so the captured graph stays valid across calls
         const ScratchSizes z = scratch_sizes(n, nnz);
@@ -1645,6 +1693,10 @@ struct Engine {
         hp->det_s = o.mid_degree;
         hp->det_m = o.hub_degree;
         hp->tail_w = o.tail_vertices;
+        const TestHooks th = test_hooks();
+        hp->bar_polls = th.barrier_polls;
+        hp->slow_block = th.slow_block;
+        hp->slow_ns = th.slow_us * 1000u;
         PGC_CUDA(cudaMemcpyAsync(problem.ptr, hp, sizeof(Problem<V>), cudaMemcpyHostToDevice,
                                  stream));
         Problem<V>* dP = problem.as<Problem<V>>();

@@ -58,6 +58,8 @@ struct State {
     unsigned long long h_next;
     unsigned long long h_first;
     unsigned long long t0;
+    unsigned long long nets_seen;      // traced: nets detection visited this round
+    unsigned long long members_seen;   // traced: their members
 };
 
 struct Problem {
@@ -75,6 +77,8 @@ struct Problem {
     long long* trace_w;
     long long* trace_s;
     long long* trace_h;
+    long long* trace_nets;
+    long long* trace_members;
     State* st;
     unsigned long long seed;
     unsigned long long timeout_ns;
@@ -367,6 +371,8 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
     int* sq = det_smem + w * kDetSmemInts;
     int* sb = sq + 32;
     int* sp = sb + 32;
+    const bool traced = P.trace_cap > 0;
+    unsigned long long seen = 0ull, seen_m = 0ull;
     for (long long b0 = ((long long)blockIdx.x * wpb + w) * 32; b0 < nn;
          b0 += (long long)gridDim.x * wpb * 32) {
         const int q = (int)b0 + lane;
@@ -374,6 +380,10 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
         if (q < nn && (all || P.net_flag[q] == r)) {
             beg = __ldg(P.m_ptr + q);
             m = __ldg(P.m_ptr + q + 1) - beg + self;
+        }
+        if (traced && q < nn && (all || P.net_flag[q] == r)) {
+            seen += 1ull;
+            seen_m += (unsigned long long)m;
         }
         const bool small = m >= 2 && m <= 32;
         const unsigned sm = __ballot_sync(kFullMask, small);
@@ -461,6 +471,14 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
         }
         __syncwarp();
     }
+    if (traced) {
+        seen = warp_sum(seen);
+        seen_m = warp_sum(seen_m);
+        if (lane == 0 && seen) {
+            atomicAdd(&P.st->nets_seen, seen);
+            atomicAdd(&P.st->members_seen, seen_m);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -478,6 +496,12 @@ __device__ void round_control(const Problem& P, cudaGraphConditionalHandle h, in
         P.trace_h[r] = (long long)*(volatile unsigned long long*)&st->h_next;
     }
     if (r == 1 && P.trace_cap > 0) P.trace_h[0] = (long long)st->h_first;
+    if (r - 1 < P.trace_cap) {
+        P.trace_nets[r - 1] = (long long)*(volatile unsigned long long*)&st->nets_seen;
+        P.trace_members[r - 1] = (long long)*(volatile unsigned long long*)&st->members_seen;
+    }
+    st->nets_seen = 0ull;
+    st->members_seen = 0ull;
     int done = 0;
     int status = *(volatile int*)&st->status;
     if (status != ST_OK) {
@@ -721,8 +745,20 @@ struct Input {
     int* col;
 };
 
+static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const Opts& o,
+                              cudaStream_t stream, int* rounds, int* num_colors);
+
+// Out of device memory: keep no half-grown scratch (the next call allocates
+// again).
 static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o,
                       cudaStream_t stream, int* rounds, int* num_colors) {
+    pgc_status s = run_scratch(cx, in, seed, o, stream, rounds, num_colors);
+    if (s == PGC_ERR_OOM) cx.release();
+    return s;
+}
+
+static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const Opts& o,
+                              cudaStream_t stream, int* rounds, int* num_colors) {
     const int n = in.n;
     if (pgc_status s = cx.key.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.lose.ensure((size_t)n * 4)) return s;
@@ -736,8 +772,8 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     const int want_trace = o.profile && o.profile->trace_cap > 0 ? o.profile->trace_cap : 0;
     const int tcap = std::max(want_trace, 1);
     if (cx.trace_cap < tcap) {
-        if (pgc_status s = cx.trace.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
-        if (pgc_status s = cx.h_misc.ensure((size_t)tcap * 3 * sizeof(long long))) return s;
+        if (pgc_status s = cx.trace.ensure((size_t)tcap * 5 * sizeof(long long))) return s;
+        if (pgc_status s = cx.h_misc.ensure((size_t)tcap * 5 * sizeof(long long))) return s;
         cx.trace_cap = tcap;
     }
     Geometry g;
@@ -760,6 +796,8 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     hp->trace_w = cx.trace.as<long long>();
     hp->trace_s = hp->trace_w + tcap;
     hp->trace_h = hp->trace_s + tcap;
+    hp->trace_nets = hp->trace_h + tcap;
+    hp->trace_members = hp->trace_nets + tcap;
     hp->trace_cap = want_trace;
     hp->st = cx.state.as<State>();
     hp->seed = seed;
@@ -824,7 +862,7 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
     kt.destroy();
     PGC_CUDA(cudaMemcpyAsync(hs, cx.state.ptr, sizeof(State), cudaMemcpyDeviceToHost, stream));
     if (want_trace) {
-        PGC_CUDA(cudaMemcpyAsync(cx.h_misc.ptr, cx.trace.ptr, (size_t)tcap * 3 * sizeof(long long),
+        PGC_CUDA(cudaMemcpyAsync(cx.h_misc.ptr, cx.trace.ptr, (size_t)tcap * 5 * sizeof(long long),
                                  cudaMemcpyDeviceToHost, stream));
     }
     PGC_CUDA(cudaStreamSynchronize(stream));
@@ -832,11 +870,15 @@ static pgc_status run(Context& cx, const Input& in, uint64_t seed, const Opts& o
         const long long* tw = cx.h_misc.as<long long>();
         const long long* ts = tw + tcap;
         const long long* th = ts + tcap;
+        const long long* tn = th + tcap;
+        const long long* tm = tn + tcap;
         const int nr = std::min(hs->round, want_trace);
         for (int i = 0; i < want_trace; ++i) {
             if (o.profile->trace_w) o.profile->trace_w[i] = i < nr ? tw[i] : 0;
             if (o.profile->trace_s) o.profile->trace_s[i] = i < nr ? ts[i] : 0;
             if (o.profile->trace_h) o.profile->trace_h[i] = i < nr ? th[i] : 0;
+            if (o.profile->trace_nets) o.profile->trace_nets[i] = i < nr ? tn[i] : 0;
+            if (o.profile->trace_members) o.profile->trace_members[i] = i < nr ? tm[i] : 0;
         }
     }
     *rounds = hs->round;
@@ -903,6 +945,7 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
         hp->ww[q] = ww + (size_t)q * n;
     }
     hp->trace_w = hp->trace_s = hp->trace_h = cx.trace.as<long long>();
+    hp->trace_nets = hp->trace_members = cx.trace.as<long long>();
     hp->trace_cap = 0;
     hp->st = cx.state.as<State>();
     hp->seed = seed;
@@ -1026,6 +1069,15 @@ static pgc_status color(int kind, int32_t n_rows, int32_t n_cols, const int32_t*
             if (pgc_status s = stage(*cx, 3, row_idx, nnz, stream, &in.r_idx)) return s;
         } else {
             in.r_idx = row_idx;
+        }
+    }
+    if (o.flags & PGC_VALIDATE) {
+        if (kind == 2) {
+            if (pgc_status s = validate::symmetric_csr(in.m_ptr, in.m_idx, n_rows, dev, stream))
+                return s;
+        } else if (pgc_status s = validate::csr_csc_pair(in.m_ptr, in.m_idx, n_rows, in.r_ptr,
+                                                         in.r_idx, n_cols, dev, stream)) {
+            return s;
         }
     }
     const bool host_col = is_host_pointer(colors);

@@ -11,9 +11,14 @@
 // worklists, round state) lives in one file-scope __device__ array of fixed
 // size, which every GPU that loads the library keeps until the process
 // exits.  The caller still passes the graph and the output in device memory.
-// The kernels are the same as pgc_color_d1's; the rounds are driven from the
-// host (one small device-to-host read per round), so no CUDA graph is built.
+// The kernels are the same as pgc_color_d1's, with its default detection
+// tiers; the rounds are driven from the host (one small device-to-host read
+// per round), so no CUDA graph is built, and the core phase (a cooperative
+// launch for the last rounds) is not used: every round runs the per-round
+// kernels, which give the same colors.
 #include "d1_engine.cuh"
+
+#include <cuda.h>
 
 namespace pgc {
 namespace d1 {
@@ -50,20 +55,54 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char* g_noalloc_ptr[kMaxDevices];
+static CUcontext g_noalloc_ctx[kMaxDevices];
 
-// Once per device, with that device current: resolve the array's address.
+// Once per device (and context), with that device current: resolve the
+// array's address.  The address is cached with the context it belongs to,
+// so a new context on the device (after cudaDeviceReset, or a context the
+// caller made current) resolves it again.
+// The current driver context, through the runtime's driver entry point (the
+// library does not link the driver library itself); nullptr if unavailable.
+static CUcontext current_context() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    static GetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetCurrent>(f);
+    }();
+    CUcontext ctx = nullptr;
+    if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
+    return ctx;
+}
+
 static pgc_status noalloc_scratch(int device, unsigned char** out) {
     if (device < 0 || device >= kMaxDevices)
         return fail(PGC_ERR_INVALID_ARG, "device ordinal out of range for the no-alloc scratch");
-    if (!g_noalloc_ptr[device]) {
+    CUcontext ctx = current_context();
+    if (!g_noalloc_ptr[device] || !ctx || ctx != g_noalloc_ctx[device]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
         g_noalloc_ptr[device] = static_cast<unsigned char*>(p);
+        g_noalloc_ctx[device] = ctx ? ctx : current_context();
     }
     *out = g_noalloc_ptr[device];
     return PGC_OK;
 }
+
+// Once work is enqueued on the shared array, every exit waits for it, so that
+// the next call (which may use another stream) never overlaps it.
+struct DrainOnExit {
+    cudaStream_t stream;
+    bool armed = false;
+    ~DrainOnExit() {
+        if (armed) cudaStreamSynchronize(stream);
+    }
+};
 
 static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                 uint64_t seed, int32_t* colors, int32_t* rounds,
@@ -128,9 +167,15 @@ static pgc_status color_noalloc(int32_t n, const int32_t* row_ptr, const int32_t
     hp.n = n;
     hp.use_deg = (flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
     hp.max_rounds = n + 1;
-    hp.det_s = 32;
-    hp.det_m = 1024;
+    const Opts defaults;
+    hp.det_s = defaults.mid_degree;
+    hp.det_m = defaults.hub_degree;
+    hp.tail_w = 0;
+    hp.bar_polls = 1u << 22;
+    hp.slow_block = -1;
     auto* dP = reinterpret_cast<Problem<SingleView>*>(base + L::problem);
+    DrainOnExit drain{stream};
+    drain.armed = true;
     PGC_CUDA(cudaMemcpyAsync(dP, &hp, sizeof hp, cudaMemcpyHostToDevice, stream));
     // The array keeps the previous call's contents: the round state must
     // start at zero; every other buffer is written before it is read.

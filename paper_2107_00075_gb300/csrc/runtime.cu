@@ -24,10 +24,31 @@ pgc_status cuda_fail(cudaError_t e, const char* what) {
     return fail(PGC_ERR_CUDA, m);
 }
 
+static std::mutex g_hooks_mu;
+static TestHooks g_hooks;
+
+TestHooks test_hooks() {
+    std::lock_guard<std::mutex> lk(g_hooks_mu);
+    return g_hooks;
+}
+
+bool test_take_alloc_failure() {
+    std::lock_guard<std::mutex> lk(g_hooks_mu);
+    if (g_hooks.fail_alloc_after < 0) return false;
+    if (g_hooks.fail_alloc_after == 0) {
+        g_hooks.fail_alloc_after = -1;
+        return true;
+    }
+    g_hooks.fail_alloc_after -= 1;
+    return false;
+}
+
 pgc_status DevBuf::ensure(size_t need) {
     if (need <= bytes && ptr) return PGC_OK;
     release();
     size_t sz = need < 256 ? 256 : need;
+    if (test_take_alloc_failure())
+        return fail(PGC_ERR_OOM, "cudaMalloc: injected allocation failure (pgc_test_fail_alloc)");
     cudaError_t e = cudaMalloc(&ptr, sz);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -185,6 +206,22 @@ const char* pgc_version(void) { return "pgc 0.1.0 (sm_103a)"; }
 
 pgc_status pgc_release(void) {
     for (auto& f : pgc::release_hooks()) f();
+    return PGC_OK;
+}
+
+pgc_status pgc_test_fail_alloc(int32_t after) {
+    std::lock_guard<std::mutex> lk(pgc::g_hooks_mu);
+    pgc::g_hooks.fail_alloc_after = after < 0 ? -1 : after;
+    return PGC_OK;
+}
+
+pgc_status pgc_test_core_barrier(uint32_t polls, int32_t slow_block, uint32_t slow_us) {
+    if (slow_us > 2000000u)
+        return pgc::fail(PGC_ERR_INVALID_ARG, "pgc_test_core_barrier: slow_us above 2 s");
+    std::lock_guard<std::mutex> lk(pgc::g_hooks_mu);
+    pgc::g_hooks.barrier_polls = polls == 0 ? (1u << 22) : polls;
+    pgc::g_hooks.slow_block = slow_block;
+    pgc::g_hooks.slow_us = slow_block < 0 ? 0u : slow_us;
     return PGC_OK;
 }
 

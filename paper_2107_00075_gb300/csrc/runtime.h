@@ -43,6 +43,16 @@ struct HostBuf {
 // host allocation); false for device or managed memory.
 bool is_host_pointer(const void* p);
 
+// Fault-injection settings of the test hooks (pgc_test_* in pgc.h).
+struct TestHooks {
+    int fail_alloc_after = -1;          // allocations left before one fails (-1: off)
+    unsigned barrier_polls = 1u << 22;  // core-loop grid barrier: polls before giving up
+    int slow_block = -1;                // core loop: this block arrives late (-1: none)
+    unsigned slow_us = 0;               // ... by this many microseconds
+};
+TestHooks test_hooks();                 // a snapshot
+bool test_take_alloc_failure();         // true if this allocation must fail
+
 // Effective options (defaults filled in).
 struct Opts {
     uint32_t flags = 0;
@@ -74,6 +84,17 @@ struct KernelTimer {
     pgc_status end();
     void destroy();
 };
+
+// PGC_VALIDATE checks (validate.cu): offsets and id ranges, and
+// symmetric_csr: the graph is symmetric (as a multiset of entries);
+// csr_csc_pair: the CSR and the CSC hold the same (row, column) pairs.
+// PGC_ERR_INVALID_ARG with a message on the first failed check.
+namespace validate {
+pgc_status symmetric_csr(const int* rp, const int* ci, int n, const DeviceInfo& dev,
+                         cudaStream_t stream);
+pgc_status csr_csc_pair(const int* rp, const int* ci, int n_rows, const int* cp, const int* ri,
+                        int n_cols, const DeviceInfo& dev, cudaStream_t stream);
+}  // namespace validate
 
 // Partial distance-2 engine slots for the server (net.cu).
 namespace net {

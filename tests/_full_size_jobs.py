@@ -4,6 +4,7 @@ import oracle
 from paper_2107_00075_gb300 import inputs as gen
 
 import hashlib
+import time
 
 import numpy as np
 
@@ -37,7 +38,12 @@ def make_input(kind):
 
 
 def oracle_job(kind):
+    """The oracle on a full-size input: (colors, rounds, num_colors, trace_w,
+    trace_s, {seconds, units}) -- the wall time of the coloring alone, the
+    input generated before the clock starts; units = edges (D1, D2: nnz / 2)
+    or entries (PD2: nnz)."""
     x = make_input(kind)
+    t0 = time.perf_counter()
     if kind == "rmat24_d1":
         r = oracle.color_d1(x.row_ptr, x.col_idx, seed=1)
     elif kind == "stencil128_d2":
@@ -45,4 +51,7 @@ def oracle_job(kind):
     else:
         r = oracle.color_pd2(x.n_rows, x.n_cols, x.row_ptr, x.col_idx, x.col_ptr, x.row_idx,
                              seed=1)
-    return r.colors, r.rounds, r.num_colors, r.trace_w, r.trace_s
+    secs = time.perf_counter() - t0
+    units = x.nnz if kind == "bip_pd2" else x.nnz / 2
+    return r.colors, r.rounds, r.num_colors, r.trace_w, r.trace_s, {"seconds": secs,
+                                                                      "units": units}

@@ -14,27 +14,69 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_design_bytes_on_a_hand_trace():
-    # three rounds: |W| = 10, 6, 2; S = 40, 30, 8; H = 20, 12, 4; n = 10, nnz = 40
+    # three rounds: |W| = 10, 6, 2; S = 40, 30, 8; H = 20, 12, 4; n = 10, nnz = 40,
+    # every degree 4 (no overflow bitmaps, no long rows)
     w, s, h = [10, 6, 2], [40, 30, 8], [20, 12, 4]
-    b = bench.d1_algorithmic_bytes(w, s, h, 10, 40)
-    assert b["d1_classify"] == 4 * 11 + 24 * 10
-    assert b["d1_build"] == 16 * 10 + 8 * 40 + 4 * 20
-    assert b["d1_tier"] == 8 * 10
-    assert b["d1_assign"] == 16 * 6 + 16 * 2          # no assign in round 1
-    assert b["d1_detect"] == 20 * (10 + 6 + 2) + 8 * (20 + 12 + 4)
-    # pushes: adjacency of each round's winners, S_r - S_{r+1}
-    assert b["d1_push"] == 12 * ((40 - 30) + (30 - 8) + 8)
+    b = bench.d1_algorithmic_bytes(w, s, h, 10, 40, deg=[4] * 10)
+    # offsets, degree/color/list-length writes, forbidden word, uncolored
+    # bitmap, one 16-byte worklist entry per vertex
+    assert b["d1_classify"] == 4 * 11 + 12 * 10 + 8 * 10 + 10 / 8 + 16 * 10
+    # entries, adjacency + neighbor degree, kept list entries, list lengths
+    assert b["d1_build"] == 16 * 10 + 8 * 40 + 4 * 20 + 4 * 10
+    assert b["d1_tier"] == 4 * 10 + 4 * 11 + 16 * 10
+    # 16-byte entry, own color, forbidden word, color write; none in round 1
+    assert b["d1_assign"] == 32 * 6 + 32 * 2
+    # entry + own color per vertex, 8 per list entry (round 1 reads none),
+    # 8 per winner, push items (1/16 B per winner adjacency entry), and a
+    # 16-byte next-round entry per loser
+    won, won_adj, nxt = [4, 4, 2], [10, 22, 8], [6, 2, 0]
+    want = sum(20 * a + 8 * l + 8 * x + y / 16 + 16 * z
+               for a, l, x, y, z in zip(w, [0, 12, 4], won, won_adj, nxt))
+    assert b["d1_detect"] == pytest.approx(want)
+    # pushes: adjacency of each round's winners, S_r - S_{r+1}, 16 B each
+    assert b["d1_push"] == 16 * (10 + 22 + 8)
     assert "d1_core" not in b
+
+
+def test_setup_bytes_count_overflow_clears_and_long_rows():
+    # one vertex of degree 70 (overflow bitmap of 3 words), one of degree 600
+    # (19 words, and two 512-entry build items instead of a worklist entry)
+    deg = [70, 600] + [1] * 8
+    b = bench.d1_setup_bytes(10, sum(deg), 0, deg)
+    clears = 4 * 3 + 4 * 19
+    assert b["d1_classify"] == 4 * 11 + 12 * 10 + 8 * 10 + 10 / 8 + 16 * 9 + 8 * 2 + clears
+    assert b["d1_build"] == 16 * 9 + 8 * 2 + 8 * sum(deg) + 4 * 10
 
 
 def test_design_bytes_split_at_the_core_phase():
     w, s, h = [10, 6, 2], [40, 30, 8], [20, 12, 4]
     whole = bench.d1_algorithmic_bytes(w, s, h, 10, 40)
     split = bench.d1_algorithmic_bytes(w, s, h, 10, 40, tail_at=2)
-    assert split["d1_detect"] == 20 * (10 + 6) + 8 * (20 + 12)
-    total = lambda d: sum(d[k] for k in ("d1_assign", "d1_detect", "d1_push", "d1_core")
-                          if k in d)
-    assert total(split) == pytest.approx(total(whole))
+    asg, det, psh = bench.d1_round_bytes(w, s, h)
+    assert split["d1_detect"] == pytest.approx(det[0] + det[1])
+    # the core phase: extraction (24 B per adjacency entry of W_3) + round 3
+    assert split["d1_core"] == pytest.approx(24 * 8 + asg[2] + det[2] + psh[2])
+    rounds = lambda d: sum(d[k] for k in ("d1_assign", "d1_detect", "d1_push"))
+    assert rounds(split) + split["d1_core"] - 24 * 8 == pytest.approx(rounds(whole))
+
+
+def test_net_bytes_on_a_hand_trace():
+    # two rounds: |W| = 8, 3; nets of W's vertices K = 20, 9; nets visited
+    # A = 5 (all) then 4 (marking); their members M = 30, 10
+    b = bench.net_algorithmic_bytes([8, 3], [20, 9], [5, 4], [30, 10], 8, 5, 30)
+    assert b["net_init"] == 28 * 8 + 12 * 20 + 4 * 5
+    assert b["net_assign"] == (16 * 8 + 12 * 20) + (16 * 3 + 12 * 9 + 8 * 9)
+    assert b["net_detect"] == (8 * 5 + 16 * 30 + 4 * 3) + (8 * 4 + 4 * 5 + 16 * 10)
+    assert b["net_commit"] == (8 * 8 + 16 * 5 + 12 * 11 + 4 * 3) + (8 * 3 + 16 * 3 + 12 * 9)
+    assert b["method_detect"] == (8 * 5 + 12 * 30 + 4 * 3) + (8 * 4 + 12 * 10)
+
+
+def test_roofline_entry_arithmetic(tmp_path, monkeypatch):
+    r = bench.roofline_entry("k", 2.0, 4, 8e9, 1000.0, "measured", "net.cu")
+    # 2e9 bytes per launch in 0.5 ms = 4000 GB/s
+    assert r["alg_bytes_per_launch"] == 2e9 and r["avg_launch_ms"] == 0.5
+    assert r["achieved"] == pytest.approx(4000.0) and r["frac"] == pytest.approx(4.0)
+    assert r["traffic"] is None and r["dram_frac"] is None
 
 
 def test_method_bytes_on_a_hand_trace():

@@ -9,7 +9,10 @@
 The colors are compared with the oracle element by element.  The three
 oracle runs take minutes of single-threaded CPU time, so they run in
 parallel in spawned worker processes while the GPU side runs here."""
+import json
 import multiprocessing as mp
+import os
+import platform
 import time
 from concurrent.futures import ProcessPoolExecutor
 
@@ -42,8 +45,35 @@ def batch_oracle_futures():
     ex.shutdown(wait=False, cancel_futures=True)
 
 
+def _record_oracle_time(kind, want):
+    """With $PGC_ORACLE_TIMES set, add the oracle's wall time on this
+    full-size input (one thread, run beside the others in a worker process)
+    to that JSON file: the CPU baseline of the full workload."""
+    path = os.environ.get("PGC_ORACLE_TIMES")
+    if not path:
+        return
+    t = want[5]
+    d = json.load(open(path)) if os.path.exists(path) else {}
+    model = None
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu part")):
+                model = l.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    unit = "entries/s" if kind == "bip_pd2" else "edges/s"
+    d[kind] = {"seconds": round(t["seconds"], 2), "value": t["units"] / t["seconds"],
+               "unit": unit, "cores": 1, "kind": "oracle", "rounds": int(want[1]),
+               "num_colors": int(want[2]), "arch": platform.machine(), "cpu": model,
+               "nproc": os.cpu_count(),
+               "how": "tests/test_gpu_full_size.py: the oracle on the full input in a spawned "
+                      "worker, three such workers in parallel"}
+    json.dump(d, open(path, "w"), indent=1)
+
+
 def _compare(got, rounds, ncol, prof, want):
-    w_colors, w_rounds, w_ncol, w_tw, w_ts = want
+    w_colors, w_rounds, w_ncol, w_tw, w_ts = want[:5]
     assert rounds == w_rounds and ncol == w_ncol
     diff = np.count_nonzero(got != w_colors)
     assert diff == 0, f"{diff} of {len(got)} colors differ"
@@ -65,6 +95,7 @@ def test_rmat24_d1_bit_exact(oracle_futures):
     want = oracle_futures["rmat24_d1"].result()
     print(f"waited {time.time() - t0:.1f} s for the oracle")
     _compare(colors, r.rounds, r.num_colors, prof, want)
+    _record_oracle_time("rmat24_d1", want)
     assert oracle.count_improper(oracle.D1, g.row_ptr, g.col_idx, colors) == 0
     assert oracle.count_non_grundy(oracle.D1, g.row_ptr, g.col_idx, colors) == 0
 
@@ -78,7 +109,9 @@ def test_stencil128_d2_bit_exact(oracle_futures):
     r = pgc.pgc_color_d2(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(),
                          seed=1, profile=prof)
     colors = r.colors.cpu().numpy()
-    _compare(colors, r.rounds, r.num_colors, prof, oracle_futures["stencil128_d2"].result())
+    want = oracle_futures["stencil128_d2"].result()
+    _compare(colors, r.rounds, r.num_colors, prof, want)
+    _record_oracle_time("stencil128_d2", want)
     assert r.num_colors >= 27
 
 
@@ -92,7 +125,9 @@ def test_bipartite_pd2_bit_exact(oracle_futures):
     r = pgc.pgc_color_pd2(b.n_rows, b.n_cols, t(b.row_ptr), t(b.col_idx), t(b.col_ptr),
                           t(b.row_idx), seed=1, profile=prof)
     colors = r.colors.cpu().numpy()
-    _compare(colors, r.rounds, r.num_colors, prof, oracle_futures["bip_pd2"].result())
+    want = oracle_futures["bip_pd2"].result()
+    _compare(colors, r.rounds, r.num_colors, prof, want)
+    _record_oracle_time("bip_pd2", want)
     assert r.num_colors >= np.diff(b.row_ptr).max()
 
 
