@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-D1, D2, PD2 = 1, 2, 3
+D1, D2, PD2, PD2B = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +64,8 @@ def _declare(lib):
         lib.oracle_color_pd2.argtypes = [i32, i32, p, p, p, p, u64, i32, i32,
                                          p, p, p, p, p, i32]
         lib.oracle_color_pd2.restype = ctypes.c_int
+        lib.oracle_color_pd2_bipartite.argtypes = lib.oracle_color_pd2.argtypes
+        lib.oracle_color_pd2_bipartite.restype = ctypes.c_int
         for name in ("oracle_count_improper", "oracle_count_non_grundy"):
             f = getattr(lib, name)
             f.argtypes = [i32, i32, i32, p, p, p, p, p]
@@ -177,6 +179,25 @@ def color_pd2(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed=1,
                               ctypes.c_uint64(seed), int(recolor_degrees), max_rounds,
                               _ptr(colors), ctypes.byref(rounds), ctypes.byref(ncol),
                               _ptr(tw), _ptr(ts), trace_cap)
+    return _finish(rc, colors, rounds, ncol, tw, ts)
+
+
+def color_pd2_bipartite(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed=1,
+                        recolor_degrees=True, max_rounds=0, trace_cap=100000,
+                        lib=None) -> Result:
+    """PD2 over every vertex of the bipartite graph (Sec. 3.6): colors of the
+    n_cols columns (ids 0..n_cols-1) then of the n_rows rows (ids n_cols + i);
+    two vertices conflict when they share a neighbor."""
+    lib = _load(lib)
+    rp, ci, cp, ri = _i32(row_ptr), _i32(col_idx), _i32(col_ptr), _i32(row_idx)
+    colors = np.zeros(n_cols + n_rows, dtype=np.int32)
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    tw = np.zeros(trace_cap, dtype=np.int64)
+    ts = np.zeros(trace_cap, dtype=np.int64)
+    rc = lib.oracle_color_pd2_bipartite(n_rows, n_cols, _ptr(rp), _ptr(ci), _ptr(cp), _ptr(ri),
+                                        ctypes.c_uint64(seed), int(recolor_degrees), max_rounds,
+                                        _ptr(colors), ctypes.byref(rounds), ctypes.byref(ncol),
+                                        _ptr(tw), _ptr(ts), trace_cap)
     return _finish(rc, colors, rounds, ncol, tw, ts)
 
 

@@ -36,7 +36,11 @@
  *         of the bipartite matrix (PD2), computed once (Sec. 3.3);
  *       * distance-2 neighborhoods exclude the vertex itself (the formula in
  *         Sec. 2.1 is garbled; Alg. 5 is read as skipping x == v);
- *       * PD2 colors only the column vertices; rows are the shared "nets";
+ *       * PD2 colors only the column vertices; rows are the shared "nets"
+ *         (oracle_color_pd2); the paper's own PD2 colors every vertex of the
+ *         bipartite graph (Sec. 3.6), which oracle_color_pd2_bipartite
+ *         computes with vertex ids columns first, then rows (the id is the
+ *         GID of rand(GID));
  *       * self-loop entries are skipped as neighbors but counted in the
  *         degree; duplicate entries are harmless.
  *
@@ -90,13 +94,15 @@ int oracle_v_is_recolored(int32_t deg_v, uint64_t rand_v, int32_t v,
 /* "cursor" so that the first-fit step and the detection step walk the     */
 /* very same set.                                                           */
 /* ---------------------------------------------------------------------- */
-enum { KIND_D1 = 1, KIND_D2 = 2, KIND_PD2 = 3 };
+enum { KIND_D1 = 1, KIND_D2 = 2, KIND_PD2 = 3, KIND_PD2B = 4 };
 
 typedef struct {
     int kind;
     int32_t n;                 /* vertices that get colors */
     const int32_t *row_ptr, *col_idx;   /* D1/D2: the graph; PD2: rows -> columns */
     const int32_t *col_ptr, *row_idx;   /* PD2 only: columns -> rows            */
+    int32_t n_cols;            /* PD2 over all of B: vertices [0, n_cols) are the
+                                  columns, n_cols + i is row i               */
 } graph_t;
 
 /*
@@ -104,6 +110,9 @@ typedef struct {
  *   D1 : x in N(v), x != v                                    (Sec. 2.1)
  *   D2 : x in N(v) or x in N(u) for some u in N(v), x != v     (Sec. 2.1, Alg. 5)
  *   PD2: x a column sharing a row with column v, x != v        (Sec. 3.6)
+ *   PD2 over all of B (Sec. 3.6: every vertex of the bipartite graph gets a
+ *   color, two-hop conflicts only): a column as for PD2; row i (vertex
+ *   n_cols + i) has the rows sharing a column with it, as vertices n_cols + r
  * Implemented as a macro-free loop that fills a caller buffer, to keep the
  * three cases side by side.  Returns the number of entries written.
  */
@@ -124,12 +133,21 @@ static int64_t neighborhood(const graph_t *g, int32_t v, int32_t *buf)
                 if (x != v) buf[k++] = x;             /* two hops via u */
             }
         }
-    } else { /* KIND_PD2 */
+    } else if (g->kind == KIND_PD2 || v < g->n_cols) { /* a column */
         for (int32_t e = g->col_ptr[v]; e < g->col_ptr[v + 1]; ++e) {
             int32_t row = g->row_idx[e];
             for (int32_t f = g->row_ptr[row]; f < g->row_ptr[row + 1]; ++f) {
                 int32_t x = g->col_idx[f];
                 if (x != v) buf[k++] = x;
+            }
+        }
+    } else { /* KIND_PD2B, row i = v - n_cols */
+        int32_t i = v - g->n_cols;
+        for (int32_t e = g->row_ptr[i]; e < g->row_ptr[i + 1]; ++e) {
+            int32_t col = g->col_idx[e];
+            for (int32_t f = g->col_ptr[col]; f < g->col_ptr[col + 1]; ++f) {
+                int32_t r = g->row_idx[f];
+                if (r != i) buf[k++] = g->n_cols + r;
             }
         }
     }
@@ -149,10 +167,16 @@ static int64_t neighborhood_capacity(const graph_t *g)
                 int32_t u = g->col_idx[e];
                 k += 1 + (g->row_ptr[u + 1] - g->row_ptr[u]);
             }
-        } else {
+        } else if (g->kind == KIND_PD2 || v < g->n_cols) {
             for (int32_t e = g->col_ptr[v]; e < g->col_ptr[v + 1]; ++e) {
                 int32_t row = g->row_idx[e];
                 k += g->row_ptr[row + 1] - g->row_ptr[row];
+            }
+        } else {
+            int32_t i = v - g->n_cols;
+            for (int32_t e = g->row_ptr[i]; e < g->row_ptr[i + 1]; ++e) {
+                int32_t col = g->col_idx[e];
+                k += g->col_ptr[col + 1] - g->col_ptr[col];
             }
         }
         if (k > best) best = k;
@@ -160,9 +184,14 @@ static int64_t neighborhood_capacity(const graph_t *g)
     return best;
 }
 
+/* deg(v): row length (D1, D2); for PD2 the vertex's degree in B: a column's
+ * CSC length, a row's CSR length (Sec. 3.3, computed once). */
 static int32_t degree_of(const graph_t *g, int32_t v)
 {
-    if (g->kind == KIND_PD2) return g->col_ptr[v + 1] - g->col_ptr[v];
+    if (g->kind == KIND_PD2 || (g->kind == KIND_PD2B && v < g->n_cols))
+        return g->col_ptr[v + 1] - g->col_ptr[v];
+    if (g->kind == KIND_PD2B)
+        return g->row_ptr[v - g->n_cols + 1] - g->row_ptr[v - g->n_cols];
     return g->row_ptr[v + 1] - g->row_ptr[v];
 }
 
@@ -302,7 +331,7 @@ int oracle_color_d1(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
 {
     if (check_csr(n, row_ptr, col_idx, n) || (n > 0 && !colors) || !rounds || !num_colors)
         return -1;
-    graph_t g = { KIND_D1, n, row_ptr, col_idx, NULL, NULL };
+    graph_t g = { KIND_D1, n, row_ptr, col_idx, NULL, NULL, 0 };
     return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
@@ -315,7 +344,7 @@ int oracle_color_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
 {
     if (check_csr(n, row_ptr, col_idx, n) || (n > 0 && !colors) || !rounds || !num_colors)
         return -1;
-    graph_t g = { KIND_D2, n, row_ptr, col_idx, NULL, NULL };
+    graph_t g = { KIND_D2, n, row_ptr, col_idx, NULL, NULL, 0 };
     return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
@@ -335,14 +364,37 @@ int oracle_color_pd2(int32_t n_rows, int32_t n_cols,
         (n_cols > 0 && !colors) || !rounds || !num_colors)
         return -1;
     if (n_rows > 0 && n_cols > 0 && row_ptr[n_rows] != col_ptr[n_cols]) return -1;
-    graph_t g = { KIND_PD2, n_cols, row_ptr, col_idx, col_ptr, row_idx };
+    graph_t g = { KIND_PD2, n_cols, row_ptr, col_idx, col_ptr, row_idx, 0 };
+    return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
+                        num_colors, trace_w, trace_s, trace_cap);
+}
+
+/* PD2 over all of B (Sec. 3.6: the method colors every vertex of the
+ * bipartite graph B(V_s, V_t, E_B)): the n_cols columns are vertices
+ * 0 .. n_cols-1 and row i is vertex n_cols + i (that vertex index is the GID
+ * in rand(GID)); two vertices conflict when they share a neighbor in B.
+ * colors: int32[n_cols + n_rows]. */
+int oracle_color_pd2_bipartite(int32_t n_rows, int32_t n_cols,
+                               const int32_t *row_ptr, const int32_t *col_idx,
+                               const int32_t *col_ptr, const int32_t *row_idx,
+                               uint64_t seed, int32_t recolor_degrees, int32_t max_rounds,
+                               int32_t *colors, int32_t *rounds, int32_t *num_colors,
+                               int64_t *trace_w, int64_t *trace_s, int32_t trace_cap)
+{
+    if (check_csr(n_rows, row_ptr, col_idx, n_cols) ||
+        check_csr(n_cols, col_ptr, row_idx, n_rows) ||
+        ((int64_t)n_cols + n_rows > INT32_MAX) ||
+        (n_cols + n_rows > 0 && !colors) || !rounds || !num_colors)
+        return -1;
+    if (n_rows > 0 && n_cols > 0 && row_ptr[n_rows] != col_ptr[n_cols]) return -1;
+    graph_t g = { KIND_PD2B, n_cols + n_rows, row_ptr, col_idx, col_ptr, row_idx, n_cols };
     return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
 
 /* ---------------------------------------------------------------------- */
-/* Checkers.  kind: 1 = D1, 2 = D2, 3 = PD2 (row/col arrays as above; for   */
-/* D1/D2 pass n_rows = n_cols = n and NULL CSC).                           */
+/* Checkers.  kind: 1 = D1, 2 = D2, 3 = PD2, 4 = PD2 over all of B (row/col  */
+/* arrays as above; for D1/D2 pass n_rows = n_cols = n and NULL CSC).      */
 /* ---------------------------------------------------------------------- */
 static int make_graph(int32_t kind, int32_t n_rows, int32_t n_cols,
                       const int32_t *row_ptr, const int32_t *col_idx,
@@ -350,13 +402,14 @@ static int make_graph(int32_t kind, int32_t n_rows, int32_t n_cols,
 {
     if (kind == KIND_D1 || kind == KIND_D2) {
         if (check_csr(n_rows, row_ptr, col_idx, n_rows)) return -1;
-        *g = (graph_t){ kind, n_rows, row_ptr, col_idx, NULL, NULL };
+        *g = (graph_t){ kind, n_rows, row_ptr, col_idx, NULL, NULL, 0 };
         return 0;
     }
-    if (kind == KIND_PD2) {
+    if (kind == KIND_PD2 || kind == KIND_PD2B) {
         if (check_csr(n_rows, row_ptr, col_idx, n_cols) ||
             check_csr(n_cols, col_ptr, row_idx, n_rows)) return -1;
-        *g = (graph_t){ kind, n_cols, row_ptr, col_idx, col_ptr, row_idx };
+        *g = (graph_t){ kind, kind == KIND_PD2 ? n_cols : n_cols + n_rows, row_ptr, col_idx,
+                        col_ptr, row_idx, n_cols };
         return 0;
     }
     return -1;

@@ -28,7 +28,28 @@ def adjacency_sets(row_ptr, col_idx):
 
 
 def neighborhoods(kind, row_ptr, col_idx, col_ptr=None, row_idx=None):
-    """S(v) for D1 ('d1'), D2 ('d2') or PD2 ('pd2', columns)."""
+    """S(v) for D1 ('d1'), D2 ('d2'), PD2 ('pd2', columns) or PD2 over every
+    vertex of the bipartite graph ('pd2b': the columns, then the rows as
+    vertices n_cols + i)."""
+    if kind == "pd2b":
+        n_cols = len(col_ptr) - 1
+        n_rows = len(row_ptr) - 1
+        cols_of = [set(int(c) for c in col_idx[row_ptr[r]:row_ptr[r + 1]]) for r in range(n_rows)]
+        rows_of = [set(col_idx_rows(col_ptr, row_idx, c)) for c in range(n_cols)]
+        out = []
+        for v in range(n_cols):
+            s = set()
+            for r in rows_of[v]:
+                s |= cols_of[r]
+            s.discard(v)
+            out.append(s)
+        for i in range(n_rows):
+            s = set()
+            for c in cols_of[i]:
+                s |= {n_cols + r for r in rows_of[c]}
+            s.discard(n_cols + i)
+            out.append(s)
+        return out
     if kind == "pd2":
         n_cols = len(col_ptr) - 1
         rows = [set(int(c) for c in col_idx[row_ptr[r]:row_ptr[r + 1]])
@@ -75,6 +96,10 @@ def _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx):
     n = len(S)
     if kind == "pd2":
         deg = [col_ptr[v + 1] - col_ptr[v] for v in range(n)]
+    elif kind == "pd2b":   # degree in the bipartite graph
+        n_cols = len(col_ptr) - 1
+        deg = ([col_ptr[v + 1] - col_ptr[v] for v in range(n_cols)] +
+               [row_ptr[i + 1] - row_ptr[i] for i in range(n - n_cols)])
     else:
         deg = [row_ptr[v + 1] - row_ptr[v] for v in range(n)]
 

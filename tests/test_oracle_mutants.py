@@ -42,8 +42,8 @@ MUTANTS = [
      "for (int32_t e = g->col_ptr[v]; e < g->col_ptr[v + 1]; ++e) {\n            int32_t row = g->row_idx[e];\n            for (int32_t f",
      "for (int32_t e = g->col_ptr[v]; e < g->col_ptr[v + 1] && e == g->col_ptr[v]; ++e) {\n            int32_t row = g->row_idx[e];\n            for (int32_t f"),
     ("pd2_degree_from_rows",
-     "if (g->kind == KIND_PD2) return g->col_ptr[v + 1] - g->col_ptr[v];",
-     "if (g->kind == KIND_PD2) return 1;"),
+     "if (g->kind == KIND_PD2 || (g->kind == KIND_PD2B && v < g->n_cols))\n        return g->col_ptr[v + 1] - g->col_ptr[v];",
+     "if (g->kind == KIND_PD2 || (g->kind == KIND_PD2B && v < g->n_cols))\n        return 1;"),
     ("d2_one_hop_dropped",
      "if (u != v) buf[k++] = u;                 /* one hop */",
      "(void)u;"),
@@ -65,10 +65,24 @@ MUTANTS = [
     ("trace_s_neighborhood_size",
      "for (int32_t i = 0; i < wn; ++i) s += deg[work[i]];",
      "for (int32_t i = 0; i < wn; ++i) s += neighborhood(g, work[i], buf);"),
+    # PD2 over every vertex of the bipartite graph
+    ("pd2b_rows_side_local_ids",
+     "rnd[v] = rand_of(seed, v);",
+     "rnd[v] = rand_of(seed, (g->kind == KIND_PD2B && v >= g->n_cols) ? v - g->n_cols : v);"),
+    ("pd2b_row_degree_wrong",
+     "return g->row_ptr[v - g->n_cols + 1] - g->row_ptr[v - g->n_cols];",
+     "return 1;"),
+    ("pd2b_row_neighbors_as_column_ids",
+     "if (r != i) buf[k++] = g->n_cols + r;",
+     "if (r != i) buf[k++] = r;"),
     ("trace_s_skips_first_entry",
      "for (int32_t i = 0; i < wn; ++i) s += deg[work[i]];",
      "for (int32_t i = 1; i < wn; ++i) s += deg[work[i]];"),
 ]
+
+
+def h(v, seed):
+    return setbased.splitmix64((seed ^ v) & setbased.MASK64)
 
 
 def _pins_pass(lib) -> bool:
@@ -106,6 +120,21 @@ def _pins_pass(lib) -> bool:
         r = oracle.color_pd2(b.n_rows, b.n_cols, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
                              seed=5, lib=lib)
         if list(r.trace_s) != [6, 3, 1]:
+            return False
+        # PD2 over all of B: the complete 3 x 4 pattern (both sides cliques,
+        # ranked by rand of their GIDs) and a hub row
+        # (with seed 1 the rows' ranks by GID 4..8 differ from those by 0..4)
+        b = _graphs.bipartite_from_rows([[0, 1, 2, 3]] * 5, 4)
+        r = oracle.color_pd2_bipartite(5, 4, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                                       seed=1, lib=lib)
+        rank = lambda ids: {v: 1 + i for i, v in enumerate(sorted(ids, key=lambda v: (h(v, 1), v)))}
+        cols, rows = rank(range(4)), rank(range(4, 9))
+        if list(r.colors) != [cols[v] for v in range(4)] + [rows[v] for v in range(4, 9)]:
+            return False
+        b = _graphs.bipartite_from_rows([[0, 1, 2, 3], [0], [1], [2], [3]], 4)
+        r = oracle.color_pd2_bipartite(5, 4, b.row_ptr, b.col_idx, b.col_ptr, b.row_idx,
+                                       seed=2, lib=lib)   # rand ranks the hub row last
+        if r.colors[4] != 1 or set(r.colors[5:]) != {2}:
             return False
         # K_{m,n} closed form and the D2 = D1(G^2) reduction
         g = gen.complete_bipartite(3, 7)
