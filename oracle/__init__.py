@@ -64,6 +64,8 @@ def _declare(lib):
         lib.oracle_color_pd2.argtypes = [i32, i32, p, p, p, p, u64, i32, i32,
                                          p, p, p, p, p, i32]
         lib.oracle_color_pd2.restype = ctypes.c_int
+        lib.oracle_color_d1_priority.argtypes = sig
+        lib.oracle_color_d1_priority.restype = ctypes.c_int
         lib.oracle_color_pd2_bipartite.argtypes = lib.oracle_color_pd2.argtypes
         lib.oracle_color_pd2_bipartite.restype = ctypes.c_int
         for name in ("oracle_count_improper", "oracle_count_non_grundy"):
@@ -145,6 +147,28 @@ def _finish(rc, colors, rounds, ncol, tw, ts):
 def color_d1(row_ptr, col_idx, seed=1, recolor_degrees=True, max_rounds=0,
              trace_cap=100000, lib=None) -> Result:
     return _color(D1, row_ptr, col_idx, seed, recolor_degrees, max_rounds, trace_cap, lib)
+
+
+PRIO_DYNAMIC, PRIO_SATURATION = 1, 2
+
+
+def color_d1_priority(row_ptr, col_idx, mode, seed=1, max_rounds=0, trace_cap=100000,
+                      lib=None) -> Result:
+    """D1 whose Alg. 4 degree term is the dynamic degree (mode 1: uncolored
+    adjacency entries) or the saturation degree (mode 2: distinct colors
+    1..deg+1 among colored neighbors), taken at the start of each round
+    (Sec. 3.3, closing paragraph)."""
+    lib = _load(lib)
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    n = len(rp) - 1
+    colors = np.zeros(max(n, 0), dtype=np.int32)
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    tw = np.zeros(trace_cap, dtype=np.int64)
+    ts = np.zeros(trace_cap, dtype=np.int64)
+    rc = lib.oracle_color_d1_priority(n, _ptr(rp), _ptr(ci), ctypes.c_uint64(seed), int(mode),
+                                      max_rounds, _ptr(colors), ctypes.byref(rounds),
+                                      ctypes.byref(ncol), _ptr(tw), _ptr(ts), trace_cap)
+    return _finish(rc, colors, rounds, ncol, tw, ts)
 
 
 def color_d2(row_ptr, col_idx, seed=1, recolor_degrees=True, max_rounds=0,

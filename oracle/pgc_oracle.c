@@ -196,11 +196,47 @@ static int32_t degree_of(const graph_t *g, int32_t v)
 }
 
 /* ---------------------------------------------------------------------- */
+/* Priorities that change from round to round (Sec. 3.3, closing paragraph: */
+/* a "dynamic" degree based on how many neighbors have been colored, or the */
+/* "saturation degree", how many colors the colored neighbors hold).  They   */
+/* take the place of deg() in Alg. 4; the degree-first decision stays.      */
+/* Readings (D1 only): both are taken at the start of each round;           */
+/*   dynamic:    the adjacency entries of v whose vertex is still uncolored  */
+/*               (the degree with colored neighbors removed; equal to deg(v)  */
+/*               in round 1);                                                */
+/*   saturation: the distinct colors held by colored neighbors of v, counting */
+/*               only colors 1 .. deg(v)+1 (the colors v's first fit can      */
+/*               meet; 0 in round 1).                                        */
+/* ---------------------------------------------------------------------- */
+enum { PRIO_STATIC = 0, PRIO_DYNAMIC = 1, PRIO_SATURATION = 2 };
+
+static int32_t round_priority(const graph_t *g, int32_t v, const int32_t *committed,
+                              const int32_t *deg, int32_t mode, int64_t *mark, int64_t *stamp)
+{
+    int32_t p = 0;
+    if (mode == PRIO_DYNAMIC) {
+        for (int32_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e)
+            if (committed[g->col_idx[e]] == 0) p += 1;
+        return p;
+    }
+    *stamp += 1;
+    for (int32_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+        int32_t u = g->col_idx[e];
+        int32_t c = committed[u];
+        if (u != v && c > 0 && c <= deg[v] + 1 && mark[c] != *stamp) {
+            mark[c] = *stamp;
+            p += 1;
+        }
+    }
+    return p;
+}
+
+/* ---------------------------------------------------------------------- */
 /* The round loop (Alg. 2 on one process).                                  */
 /* ---------------------------------------------------------------------- */
 static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees,
-                        int32_t max_rounds, int32_t *colors, int32_t *rounds_out,
-                        int32_t *num_colors_out, int64_t *trace_w,
+                        int32_t prio_mode, int32_t max_rounds, int32_t *colors,
+                        int32_t *rounds_out, int32_t *num_colors_out, int64_t *trace_w,
                         int64_t *trace_s, int32_t trace_cap)
 {
     const int32_t n = g->n;
@@ -213,6 +249,8 @@ static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees
     int32_t *committed = calloc((size_t)n, sizeof(int32_t)); /* 0 = uncolored */
     int32_t *tent = calloc((size_t)n, sizeof(int32_t));
     int32_t *deg = malloc((size_t)n * sizeof(int32_t));
+    int32_t *key = malloc((size_t)n * sizeof(int32_t));   /* the degree term of Alg. 4 */
+    int64_t *pmark = calloc((size_t)n + 2, sizeof(int64_t));
     uint64_t *rnd = malloc((size_t)n * sizeof(uint64_t));
     int32_t *work = malloc((size_t)n * sizeof(int32_t));
     int32_t *next = malloc((size_t)n * sizeof(int32_t));
@@ -220,17 +258,20 @@ static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees
     int32_t *buf = malloc((size_t)(cap > 0 ? cap : 1) * sizeof(int32_t));
     /* forbidden[c] == stamp marks color c as used in the current scan */
     int64_t *forbidden = calloc((size_t)n + 2, sizeof(int64_t));
-    if (!committed || !tent || !deg || !rnd || !work || !next || !lose || !buf || !forbidden) {
-        free(committed); free(tent); free(deg); free(rnd); free(work); free(next);
-        free(lose); free(buf); free(forbidden);
+    if (!committed || !tent || !deg || !key || !pmark || !rnd || !work || !next || !lose ||
+        !buf || !forbidden) {
+        free(committed); free(tent); free(deg); free(key); free(pmark); free(rnd); free(work);
+        free(next); free(lose); free(buf); free(forbidden);
         return -2;
     }
 
     /* Degrees are computed once (Sec. 3.3). */
     for (int32_t v = 0; v < n; ++v) {
         deg[v] = degree_of(g, v);
+        key[v] = deg[v];
         rnd[v] = rand_of(seed, v);
     }
+    int64_t pstamp = 0;
     int32_t wn = n;
     for (int32_t v = 0; v < n; ++v) work[v] = v;   /* every vertex starts uncolored */
 
@@ -246,6 +287,10 @@ static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees
             trace_w[r - 1] = wn;
             trace_s[r - 1] = s;
         }
+        if (prio_mode != PRIO_STATIC)
+            for (int32_t i = 0; i < wn; ++i)
+                key[work[i]] = round_priority(g, work[i], committed, deg, prio_mode, pmark,
+                                              &pstamp);
 
         /* (1) Speculative coloring: first-fit over committed colors only
          *     (Alg. 1's rule, Jacobi reading). */
@@ -273,8 +318,8 @@ static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees
                 int32_t u = buf[j];
                 int32_t cu = committed[u] > 0 ? committed[u] : tent[u];
                 if (cu == tent[v] &&
-                    oracle_v_is_recolored(deg[v], rnd[v], v, deg[u], rnd[u], u,
-                                          recolor_degrees)) {
+                    oracle_v_is_recolored(key[v], rnd[v], v, key[u], rnd[u], u,
+                                          prio_mode != PRIO_STATIC || recolor_degrees)) {
                     lose[v] = 1;
                     break;
                 }
@@ -304,7 +349,8 @@ static int color_rounds(const graph_t *g, uint64_t seed, int32_t recolor_degrees
     }
     *rounds_out = r;
     *num_colors_out = maxc;
-    free(committed); free(tent); free(deg); free(rnd); free(work); free(next);
+    free(committed); free(tent); free(deg); free(key); free(pmark); free(rnd); free(work);
+    free(next);
     free(lose); free(buf); free(forbidden);
     return status;
 }
@@ -332,8 +378,24 @@ int oracle_color_d1(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
     if (check_csr(n, row_ptr, col_idx, n) || (n > 0 && !colors) || !rounds || !num_colors)
         return -1;
     graph_t g = { KIND_D1, n, row_ptr, col_idx, NULL, NULL, 0 };
-    return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
+    return color_rounds(&g, seed, recolor_degrees, PRIO_STATIC, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
+}
+
+/* D1 with a priority that changes each round (Sec. 3.3, closing paragraph):
+ * prio_mode 1 = dynamic degree, 2 = saturation degree (readings above); the
+ * rest as oracle_color_d1 with recolorDegrees on. */
+int oracle_color_d1_priority(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                             uint64_t seed, int32_t prio_mode, int32_t max_rounds,
+                             int32_t *colors, int32_t *rounds, int32_t *num_colors,
+                             int64_t *trace_w, int64_t *trace_s, int32_t trace_cap)
+{
+    if (check_csr(n, row_ptr, col_idx, n) || (n > 0 && !colors) || !rounds || !num_colors ||
+        (prio_mode != PRIO_DYNAMIC && prio_mode != PRIO_SATURATION))
+        return -1;
+    graph_t g = { KIND_D1, n, row_ptr, col_idx, NULL, NULL, 0 };
+    return color_rounds(&g, seed, 1, prio_mode, max_rounds, colors, rounds, num_colors,
+                        trace_w, trace_s, trace_cap);
 }
 
 /* D2 (Sec. 3.5, Alg. 5 with doPartialColoring false). */
@@ -345,7 +407,7 @@ int oracle_color_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
     if (check_csr(n, row_ptr, col_idx, n) || (n > 0 && !colors) || !rounds || !num_colors)
         return -1;
     graph_t g = { KIND_D2, n, row_ptr, col_idx, NULL, NULL, 0 };
-    return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
+    return color_rounds(&g, seed, recolor_degrees, PRIO_STATIC, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
 
@@ -365,7 +427,7 @@ int oracle_color_pd2(int32_t n_rows, int32_t n_cols,
         return -1;
     if (n_rows > 0 && n_cols > 0 && row_ptr[n_rows] != col_ptr[n_cols]) return -1;
     graph_t g = { KIND_PD2, n_cols, row_ptr, col_idx, col_ptr, row_idx, 0 };
-    return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
+    return color_rounds(&g, seed, recolor_degrees, PRIO_STATIC, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
 
@@ -388,7 +450,7 @@ int oracle_color_pd2_bipartite(int32_t n_rows, int32_t n_cols,
         return -1;
     if (n_rows > 0 && n_cols > 0 && row_ptr[n_rows] != col_ptr[n_cols]) return -1;
     graph_t g = { KIND_PD2B, n_cols + n_rows, row_ptr, col_idx, col_ptr, row_idx, n_cols };
-    return color_rounds(&g, seed, recolor_degrees, max_rounds, colors, rounds,
+    return color_rounds(&g, seed, recolor_degrees, PRIO_STATIC, max_rounds, colors, rounds,
                         num_colors, trace_w, trace_s, trace_cap);
 }
 

@@ -79,19 +79,27 @@ def col_idx_rows(col_ptr, row_idx, v):
     return [int(r) for r in row_idx[col_ptr[v]:col_ptr[v + 1]]]
 
 
-def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, row_idx=None):
-    """Returns (colors, rounds, num_colors, worklist sizes per round)."""
-    colors, lists = _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx)
+def color(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None, row_idx=None,
+          priority="static"):
+    """Returns (colors, rounds, num_colors, worklist sizes per round).
+    priority (D1): "static" (the degree, computed once), "dynamic" (adjacency
+    entries whose vertex is uncolored at the start of the round) or
+    "saturation" (distinct colors 1..deg+1 held by colored neighbors at the
+    start of the round) -- Sec. 3.3's closing paragraph."""
+    colors, lists = _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx,
+                            priority)
     return colors, len(lists), max(colors, default=0), [len(w) for w in lists]
 
 
 def worklists(kind, row_ptr, col_idx, seed=1, recolor_degrees=True, col_ptr=None,
-              row_idx=None):
+              row_idx=None, priority="static"):
     """The worklist W_r of every round r = 1, 2, ... as sorted vertex lists."""
-    return _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx)[1]
+    return _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx,
+                   priority)[1]
 
 
-def _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx):
+def _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx,
+            priority="static"):
     S = neighborhoods(kind, row_ptr, col_idx, col_ptr, row_idx)
     n = len(S)
     if kind == "pd2":
@@ -103,15 +111,26 @@ def _rounds(kind, row_ptr, col_idx, seed, recolor_degrees, col_ptr, row_idx):
     else:
         deg = [row_ptr[v + 1] - row_ptr[v] for v in range(n)]
 
+    final = {}
+    prio = list(deg)
+
     def key(v):
         h = splitmix64((seed ^ v) & MASK64)
-        return (deg[v], -h, -v) if recolor_degrees else (-h, -v)
+        return (prio[v], -h, -v) if recolor_degrees or priority != "static" else (-h, -v)
 
-    final = {}
+    def round_priority(v):
+        row = [int(u) for u in col_idx[row_ptr[v]:row_ptr[v + 1]]]
+        if priority == "dynamic":
+            return sum(1 for u in row if u not in final)
+        return len({final[u] for u in row if u != v and u in final and final[u] <= deg[v] + 1})
+
     todo = set(range(n))
     lists = []
     while todo:
         lists.append(sorted(todo))
+        if priority != "static":
+            for v in todo:
+                prio[v] = round_priority(v)
         tentative = {}
         for v in todo:
             used = {final[u] for u in S[v] if u in final}

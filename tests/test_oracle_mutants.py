@@ -75,6 +75,13 @@ MUTANTS = [
     ("pd2b_row_neighbors_as_column_ids",
      "if (r != i) buf[k++] = g->n_cols + r;",
      "if (r != i) buf[k++] = r;"),
+    # round-varying priorities (Sec. 3.3, closing paragraph)
+    ("dynamic_counts_colored_neighbors",
+     "if (committed[g->col_idx[e]] == 0) p += 1;",
+     "if (committed[g->col_idx[e]] != 0) p += 1;"),
+    ("saturation_not_distinct",
+     "if (u != v && c > 0 && c <= deg[v] + 1 && mark[c] != *stamp) {",
+     "if (u != v && c > 0 && c <= deg[v] + 1) {"),
     ("trace_s_skips_first_entry",
      "for (int32_t i = 0; i < wn; ++i) s += deg[work[i]];",
      "for (int32_t i = 1; i < wn; ++i) s += deg[work[i]];"),
@@ -121,6 +128,24 @@ def _pins_pass(lib) -> bool:
                              seed=5, lib=lib)
         if list(r.trace_s) != [6, 3, 1]:
             return False
+        # round-varying priorities: the worked example (dynamic), a star
+        # (saturation), and the set-based restatement on random graphs
+        g = gen.from_edge_list(6, [(0, 1), (0, 4), (0, 5), (1, 2), (1, 3), (2, 3), (2, 4)])
+        r = oracle.color_d1_priority(g.row_ptr, g.col_idx, 1, seed=1, lib=lib)
+        if list(r.colors) != [1, 3, 1, 2, 2, 2]:
+            return False
+        g = gen.star(6)
+        r = oracle.color_d1_priority(g.row_ptr, g.col_idx, 2, seed=2, lib=lib)
+        if list(r.colors) != [2] + [1] * 6:
+            return False
+        for i in range(150):
+            g = gen.random_small(6 + i % 7, 0.25 + 0.05 * (i % 5), seed=7000 + i)
+            for mode, name in ((1, "dynamic"), (2, "saturation")):
+                r = oracle.color_d1_priority(g.row_ptr, g.col_idx, mode, seed=i, lib=lib)
+                c, rounds, k, _ = setbased.color("d1", g.row_ptr, g.col_idx, i, True,
+                                                 priority=name)
+                if list(r.colors) != c or r.rounds != rounds:
+                    return False
         # PD2 over all of B: the complete 3 x 4 pattern (both sides cliques,
         # ranked by rand of their GIDs) and a hub row
         # (with seed 1 the rows' ranks by GID 4..8 differ from those by 0..4)
