@@ -78,6 +78,29 @@ typedef enum {
                                     class, reuse the fastest (in memory, and in
                                     the file named by $PGC_TUNE_FILE if set);
                                     colors never depend on the choice */
+#define PGC_ASYNC          0x10u /* D1 (and its batched form): asynchronous
+                                    speculation, as KokkosKernels' VB_BIT colors
+                                    in place (Sec. 3.2): first fit also avoids the
+                                    tentative colors neighbors have already
+                                    written in the same round.  Conflicts are
+                                    still resolved by Alg. 4 on a snapshot, so the
+                                    result is a proper coloring with every color
+                                    at most deg(v) + 1, but it depends on timing:
+                                    NOT deterministic, and not a Grundy coloring.
+                                    The last rounds do not use the core phase. */
+#define PGC_PRIORITY_DYNAMIC    0x20u /* D1 (and batched): Alg. 4's degree term is
+                                    the "dynamic" degree of Sec. 3.3's closing
+                                    paragraph, taken at the start of each round:
+                                    v's adjacency entries whose vertex is still
+                                    uncolored.  Deterministic (an oracle mode
+                                    matches it bit for bit); detection then scans
+                                    every neighbor, and the last rounds do not use
+                                    the core phase. */
+#define PGC_PRIORITY_SATURATION 0x40u /* as PGC_PRIORITY_DYNAMIC, with the
+                                    "saturation degree": the distinct colors
+                                    1 .. deg(v)+1 held by v's colored neighbors.
+                                    The two exclude each other, PGC_ASYNC and
+                                    PGC_NO_DEGREE_RULE (PGC_ERR_INVALID_ARG). */
 
 /* Per-kernel timing and per-round trace, filled when non-NULL in pgc_opts. */
 #define PGC_MAX_KERNELS 8
@@ -178,6 +201,26 @@ pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_t *row_ptr,
                          const int32_t *row_idx, uint64_t seed, int32_t *colors,
                          int32_t *rounds, int32_t *num_colors, const pgc_opts *opts,
                          void *stream);
+
+/*
+ * Partial distance-2 coloring of EVERY vertex of the bipartite graph
+ * B(V_s, V_t, E_B) of the pattern, as the paper's PD2 does (Sec. 3.6: it
+ * colors all of B; Alg. 5 with doPartialColoring true, two-hop conflicts
+ * only): two columns sharing a row differ, and two rows sharing a column
+ * differ; a row and a column never conflict.  Arrays as pgc_color_pd2.
+ *   colors  int32[n_cols + n_rows], output: the columns' colors at [0, n_cols),
+ *           row i's color at n_cols + i
+ * Vertex index = GID in rand(GID) (Alg. 4): column j is j, row i is
+ * n_cols + i; the priority degree is the vertex's degree in B (a column's CSC
+ * length, a row's CSR length).  The columns therefore get exactly the colors
+ * pgc_color_pd2 gives them; rounds and num_colors cover both sides.
+ * Requires 2 * nnz < 2^31 and n_rows + n_cols < 2^31 - 1.  Colors up to 4096.
+ */
+pgc_status pgc_color_pd2_bipartite(int32_t n_rows, int32_t n_cols, const int32_t *row_ptr,
+                                   const int32_t *col_idx, const int32_t *col_ptr,
+                                   const int32_t *row_idx, uint64_t seed, int32_t *colors,
+                                   int32_t *rounds, int32_t *num_colors, const pgc_opts *opts,
+                                   void *stream);
 
 /*
  * Batched distance-1 coloring of G independent graphs in one launch (the

@@ -21,6 +21,9 @@ PGC_NO_DEGREE_RULE = 0x1
 PGC_VALIDATE = 0x2
 PGC_HOST_LOOP = 0x4
 PGC_AUTOTUNE = 0x8
+PGC_ASYNC = 0x10
+PGC_PRIORITY_DYNAMIC = 0x20
+PGC_PRIORITY_SATURATION = 0x40
 PGC_MAX_KERNELS = 8
 
 STATUS_NAMES = {0: "PGC_OK", 1: "PGC_ERR_INVALID_ARG", 2: "PGC_ERR_CUDA", 3: "PGC_ERR_OOM",
@@ -107,6 +110,8 @@ def lib():
         L.pgc_color_pd2.argtypes = [i32, i32, p, p, p, p, u64, p, ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_pd2.restype = ctypes.c_int
+        L.pgc_color_pd2_bipartite.argtypes = L.pgc_color_pd2.argtypes
+        L.pgc_color_pd2_bipartite.restype = ctypes.c_int
         L.pgc_color_d1_batch.argtypes = [i32, p, p, p, p, u64, p, p, p, ctypes.POINTER(i32),
                                          ctypes.POINTER(PgcOptsC), p]
         L.pgc_color_d1_batch.restype = ctypes.c_int
@@ -297,6 +302,35 @@ def pgc_color_pd2(n_rows: int, n_cols: int, row_ptr, col_idx, col_ptr, row_idx,
                                  ri.ptr if ri.n else None, ctypes.c_uint64(seed), co.ptr,
                                  ctypes.byref(rounds), ctypes.byref(ncol), ctypes.byref(o),
                                  _stream_handle(stream, dev))
+    _check(st)
+    _finish_profile(profile, keep, rounds.value)
+    return ColorResult(colors, rounds.value, ncol.value)
+
+
+def pgc_color_pd2_bipartite(n_rows: int, n_cols: int, row_ptr, col_idx, col_ptr, row_idx,
+                            seed: int = 1, colors=None, *, flags: int = 0, max_rounds: int = 0,
+                            block: int = 0, grid_per_sm: int = 0, timeout_ms: int = 0,
+                            profile: Optional[Profile] = None, stream=None) -> ColorResult:
+    """Partial distance-2 coloring of every vertex of the bipartite graph:
+    colors[:n_cols] the columns, colors[n_cols + i] row i (see pgc.h)."""
+    rp, ci = _Arr(row_ptr, "row_ptr"), _Arr(col_idx, "col_idx")
+    cp, ri = _Arr(col_ptr, "col_ptr"), _Arr(row_idx, "row_idx")
+    if rp.n != n_rows + 1 or cp.n != n_cols + 1:
+        raise ValueError("row_ptr/col_ptr sizes do not match n_rows/n_cols")
+    if colors is None:
+        colors = _alloc_colors(n_cols + n_rows, rp.device)
+    co = _Arr(colors, "colors")
+    if co.n < n_cols + n_rows:
+        raise ValueError("colors is shorter than n_cols + n_rows")
+    o, keep = _make_opts(flags, max_rounds, 0, 0, block, grid_per_sm, timeout_ms, profile)
+    rounds, ncol = ctypes.c_int32(0), ctypes.c_int32(0)
+    dev = rp.device or co.device
+    with _device_ctx(dev):
+        st = lib().pgc_color_pd2_bipartite(n_rows, n_cols, rp.ptr, ci.ptr if ci.n else None,
+                                           cp.ptr, ri.ptr if ri.n else None,
+                                           ctypes.c_uint64(seed), co.ptr, ctypes.byref(rounds),
+                                           ctypes.byref(ncol), ctypes.byref(o),
+                                           _stream_handle(stream, dev))
     _check(st)
     _finish_profile(profile, keep, rounds.value)
     return ColorResult(colors, rounds.value, ncol.value)

@@ -59,6 +59,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <type_traits>
 #include <unordered_map>
 
 namespace pgc {
@@ -180,6 +181,9 @@ struct Problem {
     int trace_cap;
     int n;
     int use_deg;
+    int async_mode;    // PGC_ASYNC: first fit also avoids tentative colors written this round
+    int prio_mode;     // 0: static degree; 1: dynamic degree; 2: saturation degree
+    int* prio;         // prio_mode != 0: each vertex's priority this round
     int max_rounds;
     int det_s;
     int det_m;
@@ -201,6 +205,7 @@ __device__ __forceinline__ bool higher(int du, int u, int dv, uint64_t hv, int v
 
 __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+
 __device__ __forceinline__ long long bm_offset(long long row_begin, int v) {
     return (row_begin >> 5) + v;
 }
@@ -208,10 +213,21 @@ __device__ __forceinline__ long long bm_offset(long long row_begin, int v) {
 // Forbid color c for u (a vertex of graph g).  Setting bits of an already
 // colored vertex is harmless (its set is never read again), so colors 1..64
 // need no check and the update is a fire-and-forget reduction.
-template <class V>
+// VARYING (a priority that changes each round): also keep u's priority for
+// the next round: the dynamic degree drops by one per adjacency entry of a
+// newly colored neighbor; the saturation degree grows when c is a color u
+// had not yet seen among its colored neighbors and c <= deg(u) + 1.
+template <bool VARYING, class V>
 __device__ __forceinline__ void push_color_live(const Problem<V>& P, int u, int g, int c) {
+    if (VARYING && P.prio_mode == 1) atomicSub(P.prio + u, 1);
     if (c <= 64) {
-        atomicOr(P.bm0 + u, 1ull << (c - 1));
+        const unsigned long long bit = 1ull << (c - 1);
+        if (VARYING && P.prio_mode == 2) {
+            const unsigned long long old = atomicOr(P.bm0 + u, bit);
+            if (!(old & bit) && c - 1 <= P.deg[u]) atomicAdd(P.prio + u, 1);
+        } else {
+            atomicOr(P.bm0 + u, bit);
+        }
         return;
     }
     long long bu;
@@ -219,12 +235,20 @@ __device__ __forceinline__ void push_color_live(const Problem<V>& P, int u, int 
     P.g.row(u, g, bu, du);
     if (c - 1 > du) return;   // u's own first fit never reaches c
     const int b = c - 65;
-    atomicOr(P.bmx + bm_offset(bu, u) + (b >> 5), 1u << (b & 31));
+    if (VARYING && P.prio_mode == 2) {
+        const unsigned old = atomicOr(P.bmx + bm_offset(bu, u) + (b >> 5), 1u << (b & 31));
+        if (!(old & (1u << (b & 31)))) atomicAdd(P.prio + u, 1);
+    } else {
+        atomicOr(P.bmx + bm_offset(bu, u) + (b >> 5), 1u << (b & 31));
+    }
 }
 template <class V>
 __device__ __forceinline__ void push_color(const Problem<V>& P, int u, int g, int c) {
     // most neighbors of a late winner are colored already: skip them
-    if ((P.live[u >> 5] >> (u & 31)) & 1u) push_color_live(P, u, g, c);
+    if ((P.live[u >> 5] >> (u & 31)) & 1u) {
+        if (P.prio_mode) push_color_live<true>(P, u, g, c);
+        else push_color_live<false>(P, u, g, c);
+    }
 }
 
 // Batch bookkeeping: arr[g] = max(arr[g], val) over the lanes with pred,
@@ -261,7 +285,8 @@ __global__ void d1_classify(const Problem<V>* __restrict__ Pp) {
             P.g.local_row(v, g, r0, d);
             const long long b = P.g.begin(g, r0);
             P.deg[v] = d;
-            P.col[v] = -1;
+            P.col[v] = P.async_mode ? 0 : -1;
+            if (P.prio_mode) P.prio[v] = P.prio_mode == 1 ? d : 0;
             P.hlen[v] = 0;
             P.bm0[v] = 0ull;
             if (d >= 64) {
@@ -307,6 +332,8 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp, int 
     const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
     const int nS = st->bs, nM = st->bm, nC = st->bc;
+    // priorities that change each round: the lists hold every neighbor
+    const bool all = P.prio_mode != 0;
     unsigned long long my_h = 0ull;
 
     // long rows: one warp per 512-entry item; positions by atomicAdd
@@ -326,7 +353,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp, int 
             bool keep = false;
             if (e < e1) {
                 u = P.g.nbr(beg + e, base);
-                keep = u != v && higher(__ldg(dg + u), u, d, hv, v, base, seed, use_deg);
+                keep = u != v && (all || higher(__ldg(dg + u), u, d, hv, v, base, seed, use_deg));
             }
             const unsigned m = __ballot_sync(kFullMask, keep);
             if (m == 0u) continue;
@@ -353,7 +380,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp, int 
             bool keep = false;
             if (e < d) {
                 u = P.g.nbr(beg + e, base);
-                keep = u != v && higher(__ldg(dg + u), u, d, hv, v, base, seed, use_deg);
+                keep = u != v && (all || higher(__ldg(dg + u), u, d, hv, v, base, seed, use_deg));
             }
             const unsigned m = __ballot_sync(kFullMask, keep);
             if (keep) P.hadj[beg + pos + __popc(m & ((1u << lane) - 1u))] = u;
@@ -383,7 +410,7 @@ __global__ void __maxnreg__(40) d1_build(const Problem<V>* __restrict__ Pp, int 
             for (int j = 0; j < 4; ++j) du[j] = u[j] != v ? __ldg(dg + u[j]) : 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (u[j] != v && higher(du[j], u[j], d, hv, v, base, seed, use_deg))
+                if (u[j] != v && (all || higher(du[j], u[j], d, hv, v, base, seed, use_deg)))
                     P.hadj[beg + pos++] = u[j];
         }
         P.hlen[v] = pos;
@@ -506,6 +533,59 @@ __device__ __forceinline__ void assign_phase(const Problem<V>& P) {
     }
 }
 
+// Asynchronous speculation (PGC_ASYNC; the in-place coloring of VB_BIT in
+// KokkosKernels, Sec. 3.2): first fit avoids the committed colors of N(v)
+// and also every tentative color a neighbor has already written in this
+// round (losers were reset to 0 at the end of the previous round, so a
+// negative color is this round's).  One warp per worklist vertex scans its
+// adjacency once per 64-color window.  Which tentative colors a vertex sees
+// depends on timing, so the result is a proper coloring but not a
+// deterministic one; detection is the same snapshot rule as always.
+template <class V>
+__device__ __forceinline__ void assign_async_phase(const Problem<V>& P) {
+    State* st = P.st;
+    const int cp = *(volatile int*)&st->round & 1;
+    const int n0 = st->ns[cp], n1 = st->nm[cp], n2 = st->nl[cp];
+    const long long total = (long long)n0 + n1 + n2;
+    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * wpb;
+    for (long long i = gw; i < total; i += nw) {
+        const int4 e = i < n0 ? P.ws[cp][i]
+                     : (i < n0 + n1 ? P.wm[cp][i - n0] : P.wl[cp][i - n0 - n1]);
+        const int v = e.x, d = e.z;
+        const int g = P.g.graph(v), base = P.g.base(g);
+        const long long beg = P.g.begin(g, e.w);
+        int t = 0;
+        for (int w = 0; t == 0; ++w) {
+            unsigned long long f = 0ull;
+            if (w == 0) {
+                f = P.bm0[v];
+            } else {   // overflow bitmap words for colors 64w+1 .. 64w+64
+                const unsigned* x = P.bmx + bm_offset(beg, v);
+                const int k = 2 * (w - 1), words = (d >> 5) + 1;
+                const unsigned lo = k < words ? x[k] : 0u;
+                const unsigned hi = k + 1 < words ? x[k + 1] : 0u;
+                f = ((unsigned long long)hi << 32) | lo;
+            }
+            unsigned long long tb = 0ull;
+            for (int j = lane; j < d; j += 32) {
+                const int u = P.g.nbr(beg + j, base);
+                const int c = u != v ? *(volatile const int*)(P.col + u) : 0;
+                if (c < 0) {
+                    const int b = -c - 1 - 64 * w;
+                    if (b >= 0 && b < 64) tb |= 1ull << b;
+                }
+            }
+            const unsigned tlo = __reduce_or_sync(kFullMask, (unsigned)tb);
+            const unsigned thi = __reduce_or_sync(kFullMask, (unsigned)(tb >> 32));
+            f |= ((unsigned long long)thi << 32) | tlo;
+            if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
+        }
+        if (lane == 0) *(volatile int*)(P.col + v) = -t;
+    }
+}
+
 template <class V>
 __global__ void d1_assign(const Problem<V>* __restrict__ Pp, cudaGraphConditionalHandle h,
                           int use_cond) {
@@ -516,7 +596,8 @@ __global__ void d1_assign(const Problem<V>* __restrict__ Pp, cudaGraphConditiona
         if (use_cond) cudaGraphSetConditional(h, 0u);
         P.st->push_cnt = 0;   // the previous round's push kernel has finished
     }
-    assign_phase(P);
+    if (P.async_mode) assign_async_phase(P);
+    else assign_phase(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,12 +664,49 @@ __device__ __forceinline__ void queue_push(const Problem<V>& P, int v, int d) {
     for (int k = 0; k < nit; ++k) P.push_q[base + k] = make_int2(v, k);
 }
 
-// Warp-wide: does any of the H-list entries [b0, min(b0 + 32K, hl)) of v
-// (starting at h) currently hold color t?  K ids per lane are loaded, then
-// their K colors, so a step costs two dependent loads whatever K is.
-template <int K, class V>
+// The vertex v whose list is being checked, with what a priority that
+// changes each round needs: its priority this round and its hash.
+struct Me {
+    int v, p, base;
+    uint64_t h;
+};
+struct NoMe {};   // the static order needs nothing about v
+template <bool DYN>
+using MeOf = typename std::conditional<DYN, Me, NoMe>::type;
+
+template <class V>
+__device__ __forceinline__ Me round_me(const Problem<V>& P, int v, int g) {
+    const int base = P.g.base(g);
+    return Me{v, P.prio[v], base, prio_hash(P.seed, (uint32_t)(v - base))};
+}
+
+// Priorities that change each round (Sec. 3.3, closing paragraph): u beats v
+// when its priority this round is larger; ties go to the smaller hash, then
+// the smaller id (Alg. 4 with the priority in place of the degree).
+template <class V>
+__device__ __forceinline__ bool beats(const Problem<V>& P, int u, const Me& me) {
+    const int pu = P.prio[u];
+    if (pu != me.p) return pu > me.p;
+    const uint64_t hu = prio_hash(P.seed, (uint32_t)(u - me.base));
+    if (hu != me.h) return hu < me.h;
+    return u < me.v;
+}
+
+// u (an entry of v's list, < 0: none) holds v's tentative color t and, with
+// DYN, beats v this round.  Without DYN the list holds only neighbors with
+// priority over v (a static order), so the color alone decides.
+template <bool DYN, class V>
+__device__ __forceinline__ bool conflict(const Problem<V>& P, int u, int t, MeOf<DYN> me) {
+    if constexpr (DYN) return u >= 0 && abs(P.col[u]) == t && beats(P, u, me);
+    else return u >= 0 && abs(P.col[u]) == t;
+}
+
+// Warp-wide: does any of the list entries [b0, min(b0 + 32K, hl)) of v
+// (starting at h) conflict with v's color t?  K ids per lane are loaded,
+// then their K colors, so a step costs two dependent loads whatever K is.
+template <int K, bool DYN, class V>
 __device__ __forceinline__ bool warp_step(const Problem<V>& P, const int* h, int b0, int hl,
-                                          int t) {
+                                          int t, MeOf<DYN> me) {
     const int lane = lane_id();
     int u[K];
 #pragma unroll
@@ -598,7 +716,7 @@ __device__ __forceinline__ bool warp_step(const Problem<V>& P, const int* h, int
     }
     bool hit = false;
 #pragma unroll
-    for (int j = 0; j < K; ++j) hit |= u[j] >= 0 && abs(P.col[u[j]]) == t;
+    for (int j = 0; j < K; ++j) hit |= conflict<DYN>(P, u[j], t, me);
     return __any_sync(kFullMask, hit);
 }
 
@@ -606,27 +724,30 @@ __device__ __forceinline__ bool warp_step(const Problem<V>& P, const int* h, int
 // hadj[beg]) currently hold color t?  The steps grow 64, 128, 256, 256, ...
 // entries: most losers meet their conflict in the first step, while a
 // winner, which must read its whole list, needs few dependent steps.
-template <class V>
+template <bool DYN, class V>
 __device__ __forceinline__ bool warp_conflict(const Problem<V>& P, long long beg, int hl, int t,
-                                              int from) {
+                                              int from, MeOf<DYN> me) {
     const int* h = P.hadj + beg;
     int b0 = from;
     if (b0 < hl) {
-        if (warp_step<2>(P, h, b0, hl, t)) return true;
+        if (warp_step<2, DYN>(P, h, b0, hl, t, me)) return true;
         b0 += 64;
     }
     if (b0 < hl) {
-        if (warp_step<4>(P, h, b0, hl, t)) return true;
+        if (warp_step<4, DYN>(P, h, b0, hl, t, me)) return true;
         b0 += 128;
     }
     for (; b0 < hl; b0 += 256)
-        if (warp_step<8>(P, h, b0, hl, t)) return true;
+        if (warp_step<8, DYN>(P, h, b0, hl, t, me)) return true;
     return false;
 }
 
 // Detection, commit, compaction and inline push for one round (every block
-// of the grid takes part).
-template <class V>
+// of the grid takes part).  DYN: priorities that change each round -- the
+// lists then hold every neighbor, a neighbor holding v's color must also
+// beat v this round, and every winner's push is queued (an inline push would
+// change neighbors' priorities while others still compare them).
+template <class V, bool DYN>
 __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     State* st = P.st;
     const int r = *(volatile int*)&st->round;
@@ -646,7 +767,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
     IdxAppend app_m = {smem + warp * 2 * kIdxSlots + kIdxSlots, 0};
     // Round 1: every vertex holds tentative color 1, so v loses exactly when
     // H(v) is not empty -- no list needs to be read.
-    const bool first = r == 1;
+    const bool first = r == 1 && !P.async_mode && !DYN;
 
     // --- L tier: one block per vertex (static assignment) ---
     for (int i = blockIdx.x; i < nL; i += gridDim.x) {
@@ -655,13 +776,15 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
         const int g = P.g.graph(v);
         const long long beg = P.g.begin(g, ent.w);
         const int t = -col[v];
+        MeOf<DYN> me{};
+        if constexpr (DYN) me = round_me(P, v, g);
         bool lose = first && hl > 0;
         int nxt = !first && (int)threadIdx.x < hl ? __ldg(ha + beg + threadIdx.x) : -1;
         for (int b0 = 0; !first && b0 < hl; b0 += blockDim.x) {
             const int u = nxt;
             const int e = b0 + blockDim.x + threadIdx.x;
             nxt = e < hl ? __ldg(ha + beg + e) : -1;
-            if (__syncthreads_or(u >= 0 && abs(col[u]) == t)) {
+            if (__syncthreads_or(conflict<DYN>(P, u, t, me))) {
                 lose = true;
                 break;
             }
@@ -701,8 +824,10 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
         const int in = i + nw;
         int4 en = make_int4(-1, 0, 0, 0);
         if (in < nM) en = P.wm[cp][in];
-        bool lose = first ? hl > 0 : __any_sync(kFullMask, u0 >= 0 && abs(col[u0]) == t);
-        if (!first && !lose && hl > 32) lose = warp_conflict(P, beg, hl, t, 32);
+        MeOf<DYN> me{};
+        if constexpr (DYN) me = round_me(P, v, g);
+        bool lose = first ? hl > 0 : __any_sync(kFullMask, conflict<DYN>(P, u0, t, me));
+        if (!first && !lose && hl > 32) lose = warp_conflict<DYN>(P, beg, hl, t, 32, me);
         int gn = 0, tn = 0, un = -1;
         long long bn = 0;
         if (in < nM) {
@@ -746,6 +871,8 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
             g = P.g.graph(v);
             const long long beg = P.g.begin(g, ent.w);
             t = -col[v];
+            MeOf<DYN> me{};
+            if constexpr (DYN) me = round_me(P, v, g);
             lose = first && hl > 0;
             // four list entries, then eight at a time (ids, then their colors)
             if (!first && hl > 0) {
@@ -753,14 +880,14 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) u[j] = j < hl ? __ldg(ha + beg + j) : -1;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) lose |= u[j] >= 0 && abs(col[u[j]]) == t;
+                for (int j = 0; j < 4; ++j) lose |= conflict<DYN>(P, u[j], t, me);
             }
             for (int e = 4; !first && e < hl && !lose; e += 8) {
                 int u[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = e + j < hl ? __ldg(ha + beg + e + j) : -1;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) lose |= u[j] >= 0 && abs(col[u[j]]) == t;
+                for (int j = 0; j < 8; ++j) lose |= conflict<DYN>(P, u[j], t, me);
             }
             if (lose) {
                 my_s += (unsigned long long)d;
@@ -770,7 +897,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                 col[v] = t;
                 atomicAnd(P.live + (v >> 5), ~(1u << (v & 31)));
                 my_max = max(my_max, t);
-                if (d <= kInlinePush) {
+                if (d <= kInlinePush && !DYN) {
                     // four neighbors at a time: ids, then their uncolored
                     // bits, then the updates
                     const int base = P.g.base(g);
@@ -784,7 +911,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
                         for (int j = 0; j < 4; ++j) lw[j] = u[j] != v ? P.live[u[j] >> 5] : 0u;
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            if ((lw[j] >> (u[j] & 31)) & 1u) push_color_live(P, u[j], g, t);
+                            if ((lw[j] >> (u[j] & 31)) & 1u) push_color_live<false>(P, u[j], g, t);
                     }
                 } else {
                     queue_push(P, v, d);
@@ -812,13 +939,13 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
 
 }
 
-template <class V>
+template <class V, bool DYN = false>
 __global__ void __maxnreg__(40) d1_detect(const Problem<V>* __restrict__ Pp,
                                           cudaGraphConditionalHandle h, int use_cond) {
     extern __shared__ int smem[];
     const Problem<V>& P = *Pp;
     State* st = P.st;
-    detect_phase(P, smem);
+    detect_phase<V, DYN>(P, smem);
 
     // --- last block runs the round control ---
     __shared__ int s_last;
@@ -865,9 +992,27 @@ __device__ __forceinline__ void push_phase(const Problem<V>& P) {
     }
 }
 
+// PGC_ASYNC: the next round's worklist vertices start uncolored (0), so that
+// a negative color seen during its first fit is one written in that round.
+template <class V>
+__device__ __forceinline__ void reset_next_worklist(const Problem<V>& P) {
+    const State* st = P.st;
+    if (*(volatile const int*)&st->done) return;
+    const int p = *(volatile const int*)&st->round & 1;
+    const int n0 = st->ns[p], n1 = st->nm[p], n2 = st->nl[p];
+    const long long total = (long long)n0 + n1 + n2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int v = i < n0 ? P.ws[p][i].x
+                    : (i < n0 + n1 ? P.wm[p][i - n0].x : P.wl[p][i - n0 - n1].x);
+        P.col[v] = 0;
+    }
+}
+
 template <class V>
 __global__ void d1_push(const Problem<V>* __restrict__ Pp) {
     push_phase(*Pp);
+    if (Pp->async_mode) reset_next_worklist(*Pp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1373,6 +1518,7 @@ struct Scratch {
     int4* wl;
     int2* items;
     int2* pushq;
+    int* prio = nullptr;   // n ints, only for priorities that change each round
 };
 
 struct ScratchSizes {
@@ -1424,7 +1570,7 @@ template <class V>
 struct Engine {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf deg, hlen, hadj, bm0, bmx, live, ws, wm, wl, items, pushq, state, problem, trace;
+    DevBuf deg, hlen, hadj, bm0, bmx, live, ws, wm, wl, items, pushq, prio, state, problem, trace;
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     int last_want_trace = 0, last_tcap = 1;
@@ -1432,7 +1578,7 @@ struct Engine {
     // while the adjacency is still being uploaded)
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    int g_grid = 0, g_block = 0, g_det = 0;
+    int g_grid = 0, g_block = 0, g_det = 0, g_async = 0, g_dyn = 0;
     cudaStream_t up_stream = nullptr;             // adjacency upload
     cudaEvent_t up_fork = nullptr, up_done[kUploadChunks] = {};
 
@@ -1459,7 +1605,7 @@ struct Engine {
         destroy_graph();
         destroy_upload();
         for (DevBuf* b : {&deg, &hlen, &hadj, &bm0, &bmx, &live, &ws, &wm, &wl, &items, &pushq,
-                          &state, &problem, &trace})
+                          &prio, &state, &problem, &trace})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
         trace_cap = 0;
@@ -1477,7 +1623,7 @@ struct Engine {
         g->smem = (size_t)(o.block / 32) * 2 * kAppend4Slots * sizeof(int4);
         if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
             for (const void* f : {(const void*)d1_classify<V>, (const void*)d1_tier<V>,
-                                  (const void*)d1_detect<V>})
+                                  (const void*)d1_detect<V>, (const void*)d1_detect<V, true>})
                 PGC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)g->smem));
         }
@@ -1507,18 +1653,23 @@ struct Engine {
         return k;
     }
 
-    pgc_status build_graph(const Geometry& g) {
+    pgc_status build_graph(const Geometry& g, int async, int dyn) {
         destroy_graph();
         for (int k = 0; k < 2; ++k)
-            if (pgc_status s = build_one_graph(g, k == 0, &graph[k], &exec[k])) return s;
+            if (pgc_status s = build_one_graph(g, k == 0, async, dyn, &graph[k], &exec[k]))
+                return s;
+        g_dyn = dyn;
         g_grid = g.grid;
         g_det = g.det_grid;
         g_block = g.block;
+        g_async = async;
         return PGC_OK;
     }
 
-    pgc_status build_one_graph(const Geometry& g, bool setup, cudaGraph_t* graph_out,
-                               cudaGraphExec_t* exec_out) {
+    // Setup (optional), round 1 (assign first under PGC_ASYNC), then the
+    // WHILE node of the later rounds and the core phase.
+    pgc_status build_one_graph(const Geometry& g, bool setup, int async, int dyn,
+                               cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
         Problem<V>* dP = problem.as<Problem<V>>();
         PGC_CUDA(cudaGraphCreate(graph_out, 0));
         cudaGraph_t graph = *graph_out;
@@ -1536,12 +1687,13 @@ struct Engine {
         ms.elementSize = 4;
         ms.width = sizeof(State) / 4;
         ms.height = 1;
-        cudaGraphNode_t n_ms, n_cls, n_build, n_tier, n_det, n_push, n_loop;
+        cudaGraphNode_t n_ms, n_cls, n_build, n_tier, n_asg1, n_det, n_push, n_loop;
         if (setup) PGC_CUDA(cudaGraphAddMemsetNode(&n_ms, graph, nullptr, 0, &ms));
         cudaKernelNodeParams k_cls = knode((void*)d1_classify<V>, g, g.smem, p_args);
         cudaKernelNodeParams k_build = knode((void*)d1_build<V>, g, 0, b_args);
         cudaKernelNodeParams k_tier = knode((void*)d1_tier<V>, g, g.smem, p_args);
-        cudaKernelNodeParams k_det = knode((void*)d1_detect<V>, g, g.smem, c_args);
+        cudaKernelNodeParams k_det =
+            knode(dyn ? (void*)d1_detect<V, true> : (void*)d1_detect<V>, g, g.smem, c_args);
         k_det.gridDim = dim3(g.det_grid);
         cudaKernelNodeParams k_push = knode((void*)d1_push<V>, g, 0, p_args);
         cudaKernelNodeParams k_asg = knode((void*)d1_assign<V>, g, 0, c_args);
@@ -1549,9 +1701,14 @@ struct Engine {
             PGC_CUDA(cudaGraphAddKernelNode(&n_cls, graph, &n_ms, 1, &k_cls));
             PGC_CUDA(cudaGraphAddKernelNode(&n_build, graph, &n_cls, 1, &k_build));
             PGC_CUDA(cudaGraphAddKernelNode(&n_tier, graph, &n_build, 1, &k_tier));
-            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, &n_tier, 1, &k_det));
+        }
+        if (async) {
+            PGC_CUDA(cudaGraphAddKernelNode(&n_asg1, graph, setup ? &n_tier : nullptr,
+                                            setup ? 1 : 0, &k_asg));
+            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, &n_asg1, 1, &k_det));
         } else {
-            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, nullptr, 0, &k_det));
+            PGC_CUDA(cudaGraphAddKernelNode(&n_det, graph, setup ? &n_tier : nullptr,
+                                            setup ? 1 : 0, &k_det));
         }
         PGC_CUDA(cudaGraphAddKernelNode(&n_push, graph, &n_det, 1, &k_push));
         cudaGraphNodeParams cp = {};
@@ -1617,6 +1774,9 @@ struct Engine {
         if (pgc_status s = wl.ensure(z.list)) return s;
         if (pgc_status s = items.ensure(z.items)) return s;
         if (pgc_status s = pushq.ensure(z.pushq)) return s;
+        const bool varying = (o.flags & (PGC_PRIORITY_DYNAMIC | PGC_PRIORITY_SATURATION)) != 0;
+        if (varying)
+            if (pgc_status s = prio.ensure((size_t)std::max(n, 1) * 4)) return s;
         Scratch sc;
         sc.deg = deg.as<int>();
         sc.hlen = hlen.as<int>();
@@ -1629,6 +1789,7 @@ struct Engine {
         sc.wl = wl.as<int4>();
         sc.items = items.as<int2>();
         sc.pushq = pushq.as<int2>();
+        sc.prio = varying ? prio.as<int>() : nullptr;
         if (pgc_status s = launch(sc, view, n, nnz, d_col, g_rounds, g_colors, seed, o, stream,
                                   up))
             return s;
@@ -1643,6 +1804,15 @@ struct Engine {
     pgc_status launch(const Scratch& sc, const V& view, int n, long long nnz, int* d_col,
                       int* g_rounds, int* g_colors, uint64_t seed, const Opts& o,
                       cudaStream_t stream, const Upload* up = nullptr) {
+        const uint32_t pflags = o.flags & (PGC_PRIORITY_DYNAMIC | PGC_PRIORITY_SATURATION);
+        if (pflags == (PGC_PRIORITY_DYNAMIC | PGC_PRIORITY_SATURATION))
+            return fail(PGC_ERR_INVALID_ARG, "PGC_PRIORITY_DYNAMIC and PGC_PRIORITY_SATURATION "
+                                             "exclude each other");
+        if (pflags && (o.flags & (PGC_NO_DEGREE_RULE | PGC_ASYNC)))
+            return fail(PGC_ERR_INVALID_ARG, "a round-varying priority excludes "
+                                             "PGC_NO_DEGREE_RULE and PGC_ASYNC");
+        if (pflags && !sc.prio)
+            return fail(PGC_ERR_INVALID_ARG, "round-varying priorities need their scratch");
         if (pgc_status s = state.ensure(sizeof(State))) return s;
         if (pgc_status s = problem.ensure(sizeof(Problem<V>))) return s;
         if (pgc_status s = h_problem.ensure(sizeof(Problem<V>))) return s;
@@ -1689,10 +1859,13 @@ struct Engine {
         hp->nnz = nnz;
         hp->n = n;
         hp->use_deg = (o.flags & PGC_NO_DEGREE_RULE) ? 0 : 1;
+        hp->async_mode = (o.flags & PGC_ASYNC) ? 1 : 0;
+        hp->prio_mode = (pflags & PGC_PRIORITY_DYNAMIC) ? 1 : (pflags ? 2 : 0);
+        hp->prio = sc.prio;
         hp->max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : n);
         hp->det_s = o.mid_degree;
         hp->det_m = o.hub_degree;
-        hp->tail_w = o.tail_vertices;
+        hp->tail_w = (o.flags & PGC_ASYNC) || pflags ? 0 : o.tail_vertices;
         const TestHooks th = test_hooks();
         hp->bar_polls = th.barrier_polls;
         hp->slow_block = th.slow_block;
@@ -1703,8 +1876,10 @@ struct Engine {
 
         State* hs = h_state.as<State>();
         if (!(o.flags & PGC_HOST_LOOP)) {
-            if (!exec[0] || g_grid != g.grid || g_block != g.block || g_det != g.det_grid) {
-                if (pgc_status s = build_graph(g)) return s;
+            const int dyn = hp->prio_mode != 0;
+            if (!exec[0] || g_grid != g.grid || g_block != g.block || g_det != g.det_grid ||
+                g_async != hp->async_mode || g_dyn != dyn) {
+                if (pgc_status s = build_graph(g, hp->async_mode, dyn)) return s;
             }
             if (!up) {
                 PGC_CUDA(cudaGraphLaunch(exec[0], stream));
@@ -1762,11 +1937,15 @@ struct Engine {
                       (d1_build<V><<<g.grid, g.block, 0, stream>>>(dP, 0, INT32_MAX)));
             PGC_TIMED(2, "d1_tier", (d1_tier<V><<<g.grid, g.block, g.smem, stream>>>(dP)));
             for (int round = 1;; ++round) {
-                if (round > 1)
+                if (round > 1 || hp->async_mode)
                     PGC_TIMED(3, "d1_assign",
                               (d1_assign<V><<<g.grid, g.block, 0, stream>>>(dP, none, 0)));
                 PGC_TIMED(4, "d1_detect",
-                          (d1_detect<V><<<g.det_grid, g.block, g.smem, stream>>>(dP, none, 0)));
+                          (hp->prio_mode
+                               ? d1_detect<V, true><<<g.det_grid, g.block, g.smem, stream>>>(
+                                     dP, none, 0)
+                               : d1_detect<V><<<g.det_grid, g.block, g.smem, stream>>>(dP, none,
+                                                                                      0)));
                 PGC_TIMED(5, "d1_push", (d1_push<V><<<g.grid, g.block, 0, stream>>>(dP)));
                 PGC_CUDA(cudaMemcpyAsync(hs, state.ptr, sizeof(State), cudaMemcpyDeviceToHost,
                                          stream));

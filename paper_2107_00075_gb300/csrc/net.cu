@@ -605,12 +605,45 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
 
 
 // ---------------------------------------------------------------------------
+// PD2 over every vertex of B (Sec. 3.6): one net problem with both sides.
+// Vertices: the n_cols columns (ids 0..n_cols-1), then the rows (n_cols + i).
+// Nets: the rows (net i, members = its columns), then the columns (net
+// n_rows + c, members = its rows as vertices n_cols + r).  A column's nets
+// are its rows, a row's nets are its columns.  Two vertices share a net iff
+// they are on the same side and share a neighbor in B, so each side is
+// colored exactly as partial distance-2 asks, with GIDs spanning B.
+// ---------------------------------------------------------------------------
+__global__ void pd2b_combine(const int* __restrict__ rp, const int* __restrict__ ci, int n_rows,
+                             const int* __restrict__ cp, const int* __restrict__ ri, int n_cols,
+                             int* __restrict__ mp, int* __restrict__ mi, int* __restrict__ vp,
+                             int* __restrict__ vi) {
+    const long long nnz = rp[n_rows];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // offsets: nets (rows, then columns) and vertices (columns, then rows)
+    for (long long q = t0; q <= (long long)n_rows + n_cols; q += stride) {
+        mp[q] = q <= n_rows ? rp[q] : (int)(nnz + cp[q - n_rows]);
+        vp[q] = q <= n_cols ? cp[q] : (int)(nnz + rp[q - n_cols]);
+    }
+    // members and nets, 2 nnz entries each
+    for (long long e = t0; e < 2 * nnz; e += stride) {
+        if (e < nnz) {
+            mi[e] = ci[e];
+            vi[e] = ri[e];
+        } else {
+            mi[e] = n_cols + ri[e - nnz];
+            vi[e] = n_rows + ci[e - nnz];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf key, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col;
+    DevBuf key, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col, both[4];
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     cudaGraph_t graph = nullptr;
@@ -628,7 +661,8 @@ struct Context {
     void release() {
         destroy_graph();
         for (DevBuf* b : {&key, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
-                          &stage_col, &stage[0], &stage[1], &stage[2], &stage[3]})
+                          &stage_col, &stage[0], &stage[1], &stage[2], &stage[3], &both[0],
+                          &both[1], &both[2], &both[3]})
             b->release();
         for (HostBuf* b : {&h_problem, &h_state, &h_misc}) b->release();
         trace_cap = 0;
@@ -1027,9 +1061,14 @@ static pgc_status color(int kind, int32_t n_rows, int32_t n_cols, const int32_t*
     if (pgc_status s = read_opts(opts, &o)) return s;
     *rounds = 0;
     *num_colors = 0;
-    const int n = kind == 2 ? n_rows : n_cols;
+    if (o.flags & (PGC_ASYNC | PGC_PRIORITY_DYNAMIC | PGC_PRIORITY_SATURATION))
+        return fail(PGC_ERR_INVALID_ARG, "PGC_ASYNC and the round-varying priorities are D1 "
+                                         "options");
+    const long long n_ll = kind == 2 ? n_rows : kind == 4 ? (long long)n_cols + n_rows : n_cols;
+    if (n_ll > INT32_MAX - 1) return fail(PGC_ERR_INVALID_ARG, "n_rows + n_cols too large");
+    const int n = (int)n_ll;
     if (n == 0) return PGC_OK;
-    if (!row_ptr || !colors || (kind == 3 && !col_ptr))
+    if (!row_ptr || !colors || (kind >= 3 && !col_ptr))
         return fail(PGC_ERR_INVALID_ARG, "NULL array");
     cudaStream_t stream = (cudaStream_t)stream_v;
     DeviceInfo dev;
@@ -1043,16 +1082,18 @@ static pgc_status color(int kind, int32_t n_rows, int32_t n_cols, const int32_t*
         return s;
     if (nnz < 0) return fail(PGC_ERR_INVALID_ARG, "row_ptr[n] < 0");
     if (nnz > 0 && !col_idx) return fail(PGC_ERR_INVALID_ARG, "NULL col_idx");
-    if (kind == 3) {
+    if (kind >= 3) {
         if (pgc_status s = read_int(col_ptr, is_host_pointer(col_ptr), n_cols, &nnz_c, *cx, stream))
             return s;
         if (nnz_c != nnz) return fail(PGC_ERR_INVALID_ARG, "CSR and CSC have different nnz");
         if (nnz > 0 && !row_idx) return fail(PGC_ERR_INVALID_ARG, "NULL row_idx");
     }
+    if (kind == 4 && 2ll * nnz > (long long)INT32_MAX)
+        return fail(PGC_ERR_INVALID_ARG, "PD2 over all of B needs 2 * nnz < 2^31");
     Input in;
     in.self = kind == 2 ? 1 : 0;
     in.n = n;
-    in.n_nets = n_rows;
+    in.n_nets = kind == 4 ? n_rows + n_cols : n_rows;
     if (pgc_status s = stage(*cx, 0, row_ptr, (long long)n_rows + 1, stream, &in.m_ptr)) return s;
     if (nnz > 0) {
         if (pgc_status s = stage(*cx, 1, col_idx, nnz, stream, &in.m_idx)) return s;
@@ -1071,7 +1112,28 @@ static pgc_status color(int kind, int32_t n_rows, int32_t n_cols, const int32_t*
             in.r_idx = row_idx;
         }
     }
-    if (o.flags & PGC_VALIDATE) {
+    if (kind == 4) {
+        // the validation below reads the caller's CSR/CSC, still in in.m_*/in.r_*
+        if (o.flags & PGC_VALIDATE) {
+            if (pgc_status s = validate::csr_csc_pair(in.m_ptr, in.m_idx, n_rows, in.r_ptr,
+                                                      in.r_idx, n_cols, dev, stream))
+                return s;
+        }
+        const size_t offs = ((size_t)n_rows + n_cols + 1) * 4, ents = (size_t)std::max(nnz, 1) * 8;
+        for (int k = 0; k < 4; ++k)
+            if (pgc_status s = cx->both[k].ensure(k % 2 == 0 ? offs : ents)) return s;
+        const long long work = std::max<long long>(2ll * nnz, (long long)n_rows + n_cols + 1);
+        const int grid = (int)std::min<long long>((work + 255) / 256, (long long)dev.num_sms * 8);
+        pd2b_combine<<<grid, 256, 0, stream>>>(in.m_ptr, in.m_idx, n_rows, in.r_ptr, in.r_idx,
+                                               n_cols, cx->both[0].as<int>(),
+                                               cx->both[1].as<int>(), cx->both[2].as<int>(),
+                                               cx->both[3].as<int>());
+        PGC_CUDA(cudaGetLastError());
+        in.m_ptr = cx->both[0].as<int>();
+        in.m_idx = cx->both[1].as<int>();
+        in.r_ptr = cx->both[2].as<int>();
+        in.r_idx = cx->both[3].as<int>();
+    } else if (o.flags & PGC_VALIDATE) {
         if (kind == 2) {
             if (pgc_status s = validate::symmetric_csr(in.m_ptr, in.m_idx, n_rows, dev, stream))
                 return s;
@@ -1118,6 +1180,22 @@ extern "C" pgc_status pgc_color_pd2(int32_t n_rows, int32_t n_cols, const int32_
                                     void* stream) {
     try {
         return pgc::net::color(3, n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed, colors,
+                               rounds, num_colors, opts, stream);
+    } catch (const std::exception& e) {
+        return pgc::fail(PGC_ERR_CUDA, e.what());
+    } catch (...) {
+        return pgc::fail(PGC_ERR_CUDA, "unknown exception");
+    }
+}
+
+extern "C" pgc_status pgc_color_pd2_bipartite(int32_t n_rows, int32_t n_cols,
+                                               const int32_t* row_ptr, const int32_t* col_idx,
+                                               const int32_t* col_ptr, const int32_t* row_idx,
+                                               uint64_t seed, int32_t* colors, int32_t* rounds,
+                                               int32_t* num_colors, const pgc_opts* opts,
+                                               void* stream) {
+    try {
+        return pgc::net::color(4, n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, seed, colors,
                                rounds, num_colors, opts, stream);
     } catch (const std::exception& e) {
         return pgc::fail(PGC_ERR_CUDA, e.what());
