@@ -167,3 +167,27 @@ def test_clock_sampler_without_nvidia_smi():
     s.start()
     s.wait_first(0.1)
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_serve_plan_and_digest():
+    payloads, reqs = bench.serve_plan(50, 8, seed=3)
+    assert len(payloads) == 8 and len(reqs) == 50
+    assert all(1000 <= n <= 4_000_000 and k in ("d1", "pd2") for k, n, _ in payloads)
+    assert [r[0] for r in reqs[:16]] == payloads + payloads     # request j uses payload j mod 8
+    assert len({r[1] for r in reqs}) == 50                       # every request its own seed
+    assert bench.serve_plan(50, 8, seed=3) == (payloads, reqs)   # deterministic
+    d = bench._Digest(100)
+    a = np.arange(1, 60, dtype=np.int32)
+    b = a.copy()
+    b[[3, 7]] = b[[7, 3]]
+    assert d(a) == d(a.copy()) and d(a) != d(b)
+
+
+def test_oracle_job_small_specs():
+    secs, units, rounds, ncol = bench.oracle_job(("stencil_d1", 6, 7, 2))
+    assert units == 3 * 6 * 6 * 5          # edges of the 7-point stencil 6^3
+    assert rounds >= 1 and ncol >= 2 and secs >= 0
+    secs, units, rounds, ncol = bench.oracle_job(("bip_pd2", 300, 100))
+    assert units > 0 and ncol >= 1
+    e = bench.baseline_entry([(2.0, 100.0, 3, 4), (2.0, 300.0, 5, 6)], "edges/s", "x", cores=2)
+    assert e["value"] == pytest.approx(400.0 / 2.0) and e["cores"] == 2
