@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 SEED = 1
 RMAT = dict(a=0.57, b=0.19, c=0.19)
+SERVE_CPU_MAX_N = 200_000   # the served CPU sample skips larger requests (bounded time)
 
 
 def log(*a):
@@ -217,6 +218,26 @@ def d1_round_bytes(trace_w, trace_s, trace_h):
     det = 20.0 * w + 8.0 * lists + 8.0 * won + won_adj / 16.0 + 16.0 * wn
     psh = 16.0 * won_adj
     return asg, det, psh
+
+
+def handover_round(trace_w, threshold):
+    """Index r (0-based round) of the first round whose worklist has at most
+    `threshold` vertices (the round the engine hands to the mid loop or the
+    core phase), or None."""
+    if not threshold or threshold <= 0:
+        return None
+    return next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= threshold), None)
+
+
+def d1_split(prof, tail_w):
+    """The 0-based first round a profiled (host-loop) D1 coloring ran in the
+    core phase (its first worklist of at most tail_w vertices), or None."""
+    return handover_round(prof.trace_w, tail_w) if "d1_core" in prof.kernel_ms else None
+
+
+def d1_kernel_launches(prof):
+    """Kernels one coloring launches (the core phase is four kernels)."""
+    return int(sum(v * (4 if k == "d1_core" else 1) for k, v in prof.kernel_launches.items()))
 
 
 def d1_algorithmic_bytes(trace_w, trace_s, trace_h, n, nnz, tail_at=None, deg=None):
@@ -518,7 +539,8 @@ def run_reference(args, rank, world):
                    "n": g.n, "nnz": g.nnz, "seed": SEED},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": f"R-MAT scale {scale}, edge factor 16 (1/{2**(24-scale)} of "
-                                   f"the workload), full coloring per step", **cpu_info()},
+                                   f"the workload), full coloring per step", **cpu_info(),
+                         "full_workload_recorded": recorded_full_size_oracle().get("rmat24_d1")},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -604,8 +626,7 @@ def bench_batch(pgc, inputs, torch, dev, num_graphs, peak=None, peak_kind="measu
         G = num_graphs
         d = np.diff(b.row_ptr.astype(np.int64))
         deg = np.delete(d, b.vtx_off[1:-1] + np.arange(G - 1))
-        tw = prof.trace_w
-        tail_at = next((i for i in range(1, len(tw)) if 0 < tw[i] <= 4096), None)
+        tail_at = d1_split(prof, 4096)
         nb = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, N, E, tail_at, deg)
         top = max(prof.kernel_ms, key=prof.kernel_ms.get)
         out["roofline"] = roofline_entry(top, prof.kernel_ms[top], prof.kernel_launches[top],
@@ -1104,29 +1125,12 @@ def main():
                "calls_ms": [round(1000 * c, 2) for c in calls]}
         del h_rp, h_ci, h_col
 
-    # ---- CPU legs: the oracle on bounded samples, in spawned workers that
-    #      run while the device-timed legs below proceed ----
-    pool = None
-    futs = {}
-    serve_plan_args = (max(args.serve_requests, args.serve_sweep_requests), args.serve_payloads)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pool = CpuPool(max(1, min(8, (os.cpu_count() or 4) - 4)))
-        futs["rmat"] = [pool.submit(("rmat_d1", args.cpu_baseline_scale, args.edge_factor))]
-        futs["small"] = [pool.submit(("stencil_d1", 32, 7, 20))]
-        futs["d2"] = [pool.submit(("stencil_d2", 64))]
-        futs["pd2"] = [pool.submit(("bip_pd2", 1 << 20, 1 << 18))]
-        members = list(range(0, args.batch_graphs, 8))
-        futs["batch"] = [pool.submit(("batch_members", args.batch_graphs, members[k::4]))
-                         for k in range(4)]
-        pay, rq = serve_plan(*serve_plan_args)
-        sample = rq[:96]
-        futs["serve"] = [pool.submit(("serve_requests", sample[k::4])) for k in range(4)]
-
     # ---- roofline of the dominant kernel (host-loop mode, CUDA events) ----
     roofline = None
     kernels = {}
     trace_w = None
     step_bytes = None
+    launches_per_step = None
     deg = np.diff(g.row_ptr)
     if not args.no_profile:
         prof = pgc.Profile(trace_cap=1 << 16, launch_cap=1 << 18)
@@ -1139,9 +1143,8 @@ def main():
                       open(args.dump_profile, "w"))
         trace_w = prof.trace_w
         tail_w = 4096 if args.tail_vertices == 0 else args.tail_vertices
-        tail_at = None
-        if tail_w > 0:
-            tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
+        tail_at = d1_split(prof, tail_w)
+        launches_per_step = d1_kernel_launches(prof)
         nbytes = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, n, nnz,
                                       tail_at, deg)
         kernels = kernel_table(prof, nbytes)
@@ -1163,7 +1166,7 @@ def main():
     if rank == 0 and not args.no_small:
         sg, small, sprof = bench_small_d1(pgc, inputs, torch, dev)
         sb = d1_algorithmic_bytes(sprof.trace_w, sprof.trace_s, sprof.trace_h, sg.n, sg.nnz,
-                                  None, np.diff(sg.row_ptr))
+                                  d1_split(sprof, 4096), np.diff(sg.row_ptr))
         stop = max(sprof.kernel_ms, key=sprof.kernel_ms.get)
         small["roofline"] = roofline_entry(stop, sprof.kernel_ms[stop],
                                            sprof.kernel_launches[stop], sb[stop], peak,
@@ -1177,6 +1180,25 @@ def main():
     if rank == 0 and not args.no_batch:
         batch = bench_batch(pgc, inputs, torch, dev, args.batch_graphs, peak, peak_kind)
         log("[batch]", json.dumps({k: v for k, v in batch.items() if k != "kernels"}))
+
+    # ---- CPU legs: the oracle on bounded samples, in spawned worker processes
+    #      (after the GPU legs above, so that host-loop profiling does not
+    #      compete with them for the host cores) ----
+    pool = None
+    futs = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = CpuPool(max(1, min(8, (os.cpu_count() or 4) - 4)))
+        futs["rmat"] = [pool.submit(("rmat_d1", args.cpu_baseline_scale, args.edge_factor))]
+        futs["small"] = [pool.submit(("stencil_d1", 32, 7, 20))]
+        futs["d2"] = [pool.submit(("stencil_d2", 64))]
+        futs["pd2"] = [pool.submit(("bip_pd2", 1 << 19, 1 << 17))]
+        members = list(range(0, args.batch_graphs, 8))
+        futs["batch"] = [pool.submit(("batch_members", args.batch_graphs, members[k::4]))
+                         for k in range(4)]
+        pay, rq = serve_plan(max(args.serve_requests, args.serve_sweep_requests),
+                             args.serve_payloads)
+        sample = [x for x in rq if x[0][1] <= SERVE_CPU_MAX_N][:48]
+        futs["serve"] = [pool.submit(("serve_requests", sample[k::4])) for k in range(4)]
 
     # ---- collect the CPU legs; the multi-core leg runs alone ----
     cpu = None
@@ -1216,7 +1238,7 @@ def main():
                 extra={"full_workload_recorded": full.get("stencil128_d2")})
             net["pd2_4Mx1M"]["cpu_baseline"] = baseline_entry(
                 got["pd2"], "entries/s",
-                "PD2 on a 1,048,576 x 262,144 pattern of the same recipe (1/4)",
+                "PD2 on a 524,288 x 131,072 pattern of the same recipe (1/8)",
                 extra={"full_workload_recorded": full.get("bip_pd2")})
         if batch is not None:
             batch["cpu_baseline"] = baseline_entry(
@@ -1224,8 +1246,8 @@ def main():
                 f"({len(range(0, args.batch_graphs, 8))} graphs), 4 worker processes",
                 cores=4)
         serve_cpu = baseline_entry(got["serve"], "edges/s",
-                                   "the first 96 requests of the stream, 4 worker processes",
-                                   cores=4)
+                                   f"the first 48 requests of the stream with n <= "
+                                   f"{SERVE_CPU_MAX_N}, 4 worker processes", cores=4)
     if rank == 0 and not args.no_serve:
         sweep = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
         serve = bench_serve(pgc, inputs, torch, args.serve_requests, args.serve_payloads,
@@ -1244,13 +1266,10 @@ def main():
 
     if rank == 0:
         # classify, build, tier, then (assign,) detect, push per round until the
-        # worklist is small, then the core phase (map, scan, fill, loop)
-        tail_w = 4096 if args.tail_vertices == 0 else args.tail_vertices
-        tail_at = None
-        if trace_w is not None and tail_w > 0:
-            tail_at = next((i for i in range(1, len(trace_w)) if 0 < trace_w[i] <= tail_w), None)
-        loop_rounds = tail_at if tail_at is not None else rounds
-        launches_per_step = 3 + 3 * loop_rounds - 1 + (4 if tail_at is not None else 0)
+        # worklist is small, then the mid loop and the core phase (map, scan,
+        # fill, loop): counted from the host-loop profile of the same coloring
+        if launches_per_step is None:
+            launches_per_step = 3 + 3 * rounds - 1
         out = {
             "metric": "edges colored/s (D1, RMAT scale 24)", "value": value, "unit": "edges/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -60,6 +60,8 @@ struct State {
     unsigned long long t0;
     unsigned long long nets_seen;      // traced: nets detection visited this round
     unsigned long long members_seen;   // traced: their members
+    int max_deg;      // largest degree term of a key (sizes the 32-bit key of ck)
+    int pad2;
 };
 
 struct Problem {
@@ -67,7 +69,8 @@ struct Problem {
     const int* m_idx;
     const int* r_ptr;     // vertex -> nets
     const int* r_idx;
-    int* col;
+    int* col;                   // output colors (written at commit)
+    int2* ck;                   // per vertex {color: 0 / -tentative / committed, 32-bit key}
     unsigned long long* key;    // priority key (see net_init)
     int* lose;                  // = the round in which the vertex lost (0: never)
     int* net_flag;              // = round number while the net is active
@@ -121,7 +124,7 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
     const int warp = threadIdx.x >> 5;
     WarpAppend at = {smem + warp * 2 * kAppendSlots, 0},
                aw = {smem + warp * 2 * kAppendSlots + kAppendSlots, 0};
-    int my_bound = 0;
+    int my_bound = 0, my_deg = 0;
     unsigned long long my_h = 0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
@@ -136,6 +139,7 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
             const unsigned hi = (unsigned)(prio_hash(P.seed, (uint32_t)v) >> 32);
             P.key[v] = (P.use_deg ? (unsigned long long)d << 32 : 0ull) | (unsigned long long)~hi;
             P.col[v] = 0;
+            my_deg = max(my_deg, d);
             P.lose[v] = 0;
             k = d + P.self;
             long long b = 0;
@@ -151,9 +155,11 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < P.n_nets; q += stride)
         P.net_flag[q] = 0;
     my_bound = warp_max(my_bound);
+    my_deg = warp_max(my_deg);
     my_h = warp_sum(my_h);
     if (lane_id() == 0) {
         atomicMax(&st->bound, my_bound);
+        if (P.use_deg) atomicMax(&st->max_deg, my_deg);
         if (my_h) atomicAdd(&st->h_first, my_h);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -174,6 +180,19 @@ __device__ __forceinline__ void mark_net(const Problem& P, int q, int r) {
     if (P.net_flag[q] != r) P.net_flag[q] = r;
 }
 
+// The 32-bit key stored beside the color: key >> b, where b is the bit
+// width of the largest degree term, so the degree still dominates and the
+// top 32 - b hash bits follow.  It orders like the full key except that two
+// different keys may share it; detection resolves such ties from the full key.
+__device__ __forceinline__ unsigned key32(const Problem& P, int v, int b) {
+    return (unsigned)(__ldg(P.key + v) >> b);
+}
+
+__device__ __forceinline__ int key_shift(const State* st) {
+    const int d = *(volatile const int*)&st->max_deg;
+    return d > 0 ? 32 - __clz(d) : 0;
+}
+
 __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalHandle h,
                            int use_cond) {
     const Problem& P = *Pp;
@@ -186,6 +205,7 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
     const bool mark = *(volatile int*)&st->all_active == 0;
     const unsigned long long* mk = P.mask;
     const long long nn = P.n_nets;
+    const int kb = key_shift(st);
     // thread tier
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += stride) {
@@ -211,7 +231,7 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
             atomicExch(&st->status, ST_OVERFLOW);
             t = 64 * P.windows;
         }
-        P.col[v] = -t;
+        P.ck[v] = make_int2(-t, (int)key32(P, v, kb));
         if (mark)
             for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
     }
@@ -234,7 +254,7 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
             if (lane == 0) atomicExch(&st->status, ST_OVERFLOW);
             t = 64 * P.windows;
         }
-        if (lane == 0) P.col[v] = -t;
+        if (lane == 0) P.ck[v] = make_int2(-t, (int)key32(P, v, kb));
         if (mark)
             for (int j = lane; j < k; j += 32) mark_net(P, vertex_net(P, v, beg, j), r);
     }
@@ -302,7 +322,7 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
         unsigned long long kx = 0ull;
         if (i0 + lane < m) {
             x = net_member(P, q, i0 + lane);
-            const int cx = P.col[x];
+            const int cx = P.ck[x].x;
             c = cx < 0 ? -cx : 0;
             if (c) kx = __ldg(P.key + x);
         }
@@ -313,7 +333,7 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
             unsigned long long ky = 0ull;
             if (j0 + lane < m) {
                 y = net_member(P, q, j0 + lane);
-                const int c2 = P.col[y];
+                const int c2 = P.ck[y].x;
                 cy = c2 < 0 ? -c2 : 0;
                 if (cy) ky = __ldg(P.key + y);
             }
@@ -336,24 +356,25 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
 __device__ __forceinline__ void resolve_rows(const Problem& P, const int (&x)[kDetRows],
                                              const int (&id)[kDetRows], unsigned long long seed,
                                              int r) {
-    int cx[kDetRows];
-    unsigned long long kx[kDetRows];
+    int2 p[kDetRows];
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) p[k] = x[k] >= 0 ? P.ck[x[k]] : make_int2(0, 0);
 #pragma unroll
     for (int k = 0; k < kDetRows; ++k) {
-        cx[k] = 0;
-        kx[k] = 0ull;
-        if (x[k] >= 0) {
-            cx[k] = P.col[x[k]];
-            kx[k] = __ldg(P.key + x[k]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kDetRows; ++k) {
-        // only uncolored members can conflict
-        const int c = cx[k] < 0 ? -cx[k] : 0;
+        // only uncolored members can conflict, and only if two share a row
+        const int c = p[k].x < 0 ? -p[k].x : 0;
+        if (__popc(__ballot_sync(kFullMask, c != 0)) < 2) continue;   // warp-uniform
         const unsigned tag = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
         const unsigned g = __match_any_sync(kFullMask, tag);
-        if (c && __popc(g) > 1 && group_loses(g, x[k], kx[k], seed)) P.lose[x[k]] = r;
+        if (!c || __popc(g) < 2) continue;
+        // the group's winner: the largest 32-bit key; members sharing it are
+        // decided by the full key (then the hash and the id)
+        const unsigned k32 = (unsigned)p[k].y;
+        const unsigned m1 = __reduce_max_sync(g, k32);
+        const unsigned ties = __ballot_sync(g, k32 == m1) & g;
+        bool lose = k32 != m1;
+        if (!lose && __popc(ties) > 1) lose = group_loses(ties, x[k], __ldg(P.key + x[k]), seed);
+        if (lose) P.lose[x[k]] = r;
     }
 }
 
@@ -570,8 +591,9 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
             } else {
                 const int beg = __ldg(P.r_ptr + v);
                 const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
-                const int t = -P.col[v];
+                const int t = -P.ck[v].x;
                 P.col[v] = t;
+                reinterpret_cast<int*>(P.ck + v)[0] = t;
                 my_max = max(my_max, t);
                 const int w = (t - 1) >> 6;
                 const unsigned long long bit = 1ull << ((t - 1) & 63);
@@ -643,7 +665,7 @@ __global__ void pd2b_combine(const int* __restrict__ rp, const int* __restrict__
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf key, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col, both[4];
+    DevBuf key, ck, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col, both[4];
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     cudaGraph_t graph = nullptr;
@@ -660,7 +682,7 @@ struct Context {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&key, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
+        for (DevBuf* b : {&key, &ck, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
                           &stage_col, &stage[0], &stage[1], &stage[2], &stage[3], &both[0],
                           &both[1], &both[2], &both[3]})
             b->release();
@@ -795,6 +817,7 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
                               cudaStream_t stream, int* rounds, int* num_colors) {
     const int n = in.n;
     if (pgc_status s = cx.key.ensure((size_t)n * 8)) return s;
+    if (pgc_status s = cx.ck.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.lose.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.flag.ensure((size_t)std::max(in.n_nets, 1) * 4)) return s;
     if (pgc_status s = cx.wt.ensure((size_t)n * 4 * 2)) return s;
@@ -821,6 +844,7 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
     hp->r_idx = in.r_idx;
     hp->col = in.col;
     hp->key = cx.key.as<unsigned long long>();
+    hp->ck = cx.ck.as<int2>();
     hp->lose = cx.lose.as<int>();
     hp->net_flag = cx.flag.as<int>();
     for (int p = 0; p < 2; ++p) {
@@ -935,7 +959,8 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
 // ---------------------------------------------------------------------------
 size_t scratch_bytes(int n, int n_nets, int windows) {
     auto a = [](size_t x) { return (x + 255) / 256 * 256; };
-    return a((size_t)n * 8) + a((size_t)n * 4) + a((size_t)std::max(n_nets, 1) * 4) +
+    return a((size_t)n * 8) + a((size_t)n * 8) + a((size_t)n * 4) +
+           a((size_t)std::max(n_nets, 1) * 4) +
            a((size_t)windows * (size_t)std::max(n_nets, 1) * 8) + a((size_t)n * 8) * 2;
 }
 
@@ -945,6 +970,8 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     auto a = [](size_t x) { return (x + 255) / 256 * 256; };
     char* p = static_cast<char*>(scratch);
     unsigned long long* key = reinterpret_cast<unsigned long long*>(p);
+    p += a((size_t)n * 8);
+    int2* ck = reinterpret_cast<int2*>(p);
     p += a((size_t)n * 8);
     int* lose = reinterpret_cast<int*>(p);
     p += a((size_t)n * 4);
@@ -971,6 +998,7 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     hp->r_idx = in.r_idx;
     hp->col = in.col;
     hp->key = key;
+    hp->ck = ck;
     hp->lose = lose;
     hp->net_flag = flag;
     hp->mask = mask;

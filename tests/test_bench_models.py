@@ -191,3 +191,18 @@ def test_oracle_job_small_specs():
     assert units > 0 and ncol >= 1
     e = bench.baseline_entry([(2.0, 100.0, 3, 4), (2.0, 300.0, 5, 6)], "edges/s", "x", cores=2)
     assert e["value"] == pytest.approx(400.0 / 2.0) and e["cores"] == 2
+
+
+def test_d1_split_and_launch_count():
+    from types import SimpleNamespace
+    prof = SimpleNamespace(trace_w=[100, 60, 30, 9, 4, 1],
+                           kernel_ms={"d1_detect": 1.0, "d1_core": 1.0, "d1_assign": 1.0,
+                                      "d1_push": 1.0},
+                           kernel_launches={"d1_classify": 1, "d1_build": 1, "d1_tier": 1,
+                                            "d1_detect": 3, "d1_assign": 2, "d1_push": 3,
+                                            "d1_core": 1})
+    # rounds 1-3 launch per round, rounds 4.. in the core phase (worklist <= 10)
+    assert bench.d1_split(prof, 10) == 3
+    assert bench.d1_kernel_launches(prof) == 3 + 3 + 2 + 3 + 4
+    prof.kernel_ms.pop("d1_core")
+    assert bench.d1_split(prof, 10) is None
