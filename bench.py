@@ -298,7 +298,9 @@ def net_algorithmic_bytes(trace_w, trace_h, trace_nets, trace_members, n, n_nets
                of a worklist vertex its id 4 and mask word 8 (* windows),
                and when marking its flag read and write 8
       detect:  per visited net offsets 8 (and its flag 4 when marking); per
-               member id 4, color 4, key 8; a lose flag per loser 4
+               member id 4 and packed color and 32-bit key 8 (+ the full key 8
+               for members tied on the short key, not counted); a lose flag per
+               loser 4
       commit:  per worklist vertex entry 4, lose flag 4; per winner offsets 8,
                color read and write 8, and per net of a winner its id 4 and
                mask update 8; per loser its next-round entry 4"""
@@ -311,7 +313,7 @@ def net_algorithmic_bytes(trace_w, trace_h, trace_nets, trace_members, n, n_nets
     marking = a < n_nets
     init = 28.0 * n + 12.0 * float(k[0] if len(k) else 0.0) + 4.0 * n_nets
     asg = 16.0 * w + (4.0 + 8.0 * windows) * k + 8.0 * k * marking
-    det = 8.0 * a + 4.0 * n_nets * marking + 16.0 * m + 4.0 * wn
+    det = 8.0 * a + 4.0 * n_nets * marking + 12.0 * m + 4.0 * wn
     com = 8.0 * w + 16.0 * (w - wn) + 12.0 * (k - kn) + 4.0 * wn
     # the method's bytes for detection as the paper states it (nets with a
     # worklist member, 8 per net + 12 per member + the next worklist), for
