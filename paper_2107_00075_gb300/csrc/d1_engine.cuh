@@ -940,7 +940,7 @@ __device__ __forceinline__ void detect_phase(const Problem<V>& P, int* smem) {
 }
 
 template <class V, bool DYN = false>
-__global__ void __maxnreg__(40) d1_detect(const Problem<V>* __restrict__ Pp,
+__global__ void __maxnreg__(48) d1_detect(const Problem<V>* __restrict__ Pp,
                                           cudaGraphConditionalHandle h, int use_cond) {
     extern __shared__ int smem[];
     const Problem<V>& P = *Pp;

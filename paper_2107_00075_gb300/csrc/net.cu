@@ -267,15 +267,24 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
 //
 // Within one net, the members holding tentative color c form a group; every
 // member of the group except its highest-priority one is recolored (Alg. 4
-// applied to each pair of the group).  So a group needs no pairwise loop:
-// three warp reductions (largest degree, smallest hash, smallest id) find
-// its winner.  Small nets (2..32 members) are packed whole into "rows" of
-// 32 lanes -- several nets per row -- and four rows are loaded at once so a
-// warp keeps many independent gathers in flight.  Larger nets compare every
-// member against every other member, 32 x 32 at a time.
+// applied to each pair of the group).  So a group needs no pairwise loop: its
+// winner is the member with the largest key.  Small nets (2..32 members) are
+// packed whole into "rows" of 32 lanes -- several nets per row -- and four
+// rows are loaded at once so a warp keeps many independent gathers in
+// flight.  Within a row, match.any finds each lane's group; the group's
+// lowest lane names a shared-memory slot that every member raises to its
+// 32-bit key with one atomic max, so a row costs the same few instructions
+// however many groups it holds.  Larger nets compare every member against
+// every other member, 32 x 32 at a time.
 // ---------------------------------------------------------------------------
 constexpr int kDetRows = 4;        // rows loaded together
 constexpr int kDetSmemInts = 97;   // per warp: 32 net ids, 32 m_ptr, 33 packed starts
+constexpr int kDetSlots = kDetRows * 32;   // per warp: one max slot per lane of each row
+constexpr size_t kDetWarpBytes = kDetSlots * sizeof(unsigned) + kDetSmemInts * sizeof(int);
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ unsigned lanemask_le() {
     unsigned m;
@@ -351,65 +360,202 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
     }
 }
 
-// Loads the colors and keys of up to kDetRows rows of members (x < 0: no
-// member) and flags the losers.  id: 1 + the net's index within its row.
-__device__ __forceinline__ void resolve_rows(const Problem& P, const int (&x)[kDetRows],
-                                             const int (&id)[kDetRows], unsigned long long seed,
-                                             int r) {
+// The exact decision for one lane of a group g (two or more lanes): the
+// largest 32-bit key wins; members sharing it are decided by the full key,
+// then the hash and the id.
+__device__ __noinline__ bool group_exact(unsigned g, unsigned k32, int x,
+                                         const unsigned long long* key, unsigned long long seed) {
+    const unsigned m1 = __reduce_max_sync(g, k32);
+    const unsigned ties = __ballot_sync(g, k32 == m1) & g;
+    if (k32 != m1) return true;
+    if (__popc(ties) == 1) return false;
+    return group_loses(ties, x, __ldg(key + x), seed);
+}
+
+// What detection reads: the problem (in global memory, read through the
+// read-only path; the compiler keeps in registers what fits).
+using DetView = Problem;
+
+// The rows' tentative colors and keys.  t: the group tag (color, net in the
+// row), 0 for a lane that holds no tentative member; g: the lanes sharing it.
+struct RowState {
+    unsigned t[kDetRows], g[kDetRows], k32[kDetRows];
+};
+
+__device__ __forceinline__ void load_rows(const DetView& D, const int (&x)[kDetRows],
+                                          const int (&id)[kDetRows], RowState& S) {
     int2 p[kDetRows];
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) p[k] = x[k] >= 0 ? P.ck[x[k]] : make_int2(0, 0);
+    for (int k = 0; k < kDetRows; ++k) p[k] = x[k] >= 0 ? D.ck[x[k]] : make_int2(0, 0);
 #pragma unroll
     for (int k = 0; k < kDetRows; ++k) {
-        // only uncolored members can conflict, and only if two share a row
         const int c = p[k].x < 0 ? -p[k].x : 0;
-        if (__popc(__ballot_sync(kFullMask, c != 0)) < 2) continue;   // warp-uniform
-        const unsigned tag = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
-        const unsigned g = __match_any_sync(kFullMask, tag);
-        if (!c || __popc(g) < 2) continue;
-        // the group's winner: the largest 32-bit key; members sharing it are
-        // decided by the full key (then the hash and the id)
-        const unsigned k32 = (unsigned)p[k].y;
-        const unsigned m1 = __reduce_max_sync(g, k32);
-        const unsigned ties = __ballot_sync(g, k32 == m1) & g;
-        bool lose = k32 != m1;
-        if (!lose && __popc(ties) > 1) lose = group_loses(ties, x[k], __ldg(P.key + x[k]), seed);
-        if (lose) P.lose[x[k]] = r;
+        S.t[k] = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
+        S.g[k] = __match_any_sync(kFullMask, S.t[k]);
+        S.k32[k] = (unsigned)p[k].y;
     }
 }
 
-__global__ void net_detect(const Problem* __restrict__ Pp) {
+// Rows where two members of one group both hold the group's largest 32-bit
+// key (each row's winners outnumber its contested groups): those groups are
+// decided again from the full keys.  Rare: the 32-bit key holds the degree
+// and the top hash bits.
+__device__ __forceinline__ void settle_ties(const DetView& D, const int (&x)[kDetRows],
+                                            const RowState& S, unsigned need,
+                                            bool (&lose)[kDetRows]) {
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) {
+        if (!(need >> k & 1u)) continue;   // warp-uniform
+        const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
+        if (contested) lose[k] = group_exact(S.g[k], S.k32[k], x[k], D.key, D.seed);
+    }
+}
+
+// Group winners, one warp-wide max per contested group: the largest
+// remaining tag names the next group, a max over its members' keys its
+// winner.  A row with one contested group (every round-1 net) costs two
+// reductions.
+__device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&x)[kDetRows],
+                                                  const int (&id)[kDetRows], int r) {
+    RowState S;
+    load_rows(D, x, id, S);
+    bool lose[kDetRows];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) {
+        const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
+        unsigned rem = contested ? S.t[k] : 0u, mx = 0u;
+        int groups = 0;
+        while (__any_sync(kFullMask, rem != 0u)) {   // warp-uniform
+            const unsigned tc = __reduce_max_sync(kFullMask, rem);
+            const bool in = rem == tc;
+            const unsigned m = __reduce_max_sync(kFullMask, in ? S.k32[k] : 0u);
+            if (in) {
+                mx = m;
+                rem = 0u;
+            }
+            ++groups;
+        }
+        lose[k] = contested && S.k32[k] < mx;
+        const int winners = __popc(__ballot_sync(kFullMask, contested && S.k32[k] == mx));
+        if (winners > groups) need |= 1u << k;
+    }
+    if (need) settle_ties(D, x, S, need, lose);
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k)
+        if (lose[k]) D.lose[x[k]] = r;
+}
+
+// Group winners through shared memory: the group's lowest lane names a slot
+// that every member raises to its key with one atomic max.  The cost does
+// not grow with the number of groups in the row.  slot: this warp's
+// kDetSlots words.
+__device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (&x)[kDetRows],
+                                                   const int (&id)[kDetRows], int r,
+                                                   unsigned* slot) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) slot[k * 32 + lane] = 0u;
+    RowState S;
+    load_rows(D, x, id, S);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k)
+        if (S.t[k] && (S.g[k] & (S.g[k] - 1u)))
+            atomicMax(slot + k * 32 + (__ffs(S.g[k]) - 1), S.k32[k]);
+    __syncwarp();
+    bool lose[kDetRows];
+    unsigned need = 0u;
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k) {
+        const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
+        const int leader = __ffs(S.g[k]) - 1;
+        const unsigned mx = contested ? slot[k * 32 + leader] : 0u;
+        lose[k] = contested && S.k32[k] < mx;
+        const int winners = __popc(__ballot_sync(kFullMask, contested && S.k32[k] == mx));
+        const int groups = __popc(__ballot_sync(kFullMask, contested && leader == lane));
+        if (winners > groups) need |= 1u << k;
+    }
+    __syncwarp();
+    if (need) settle_ties(D, x, S, need, lose);
+#pragma unroll
+    for (int k = 0; k < kDetRows; ++k)
+        if (lose[k]) D.lose[x[k]] = r;
+}
+
+#ifndef PGC_PACKED_SLOTS
+#define PGC_PACKED_SLOTS 1
+#endif
+
+__global__ void __maxnreg__(48) net_detect(const Problem* __restrict__ Pp) {
     // per warp: the tile's small active nets, compacted (net id, m_ptr,
     // start of the net in the packed tile)
-    extern __shared__ int det_smem[];
+    extern __shared__ unsigned det_smem[];
     const Problem& P = *Pp;
     const int r = *(volatile int*)&P.st->round;
     const bool all = *(volatile int*)&P.st->all_active != 0;
     const int lane = lane_id(), wpb = blockDim.x >> 5, w = threadIdx.x >> 5;
-    const unsigned long long seed = P.seed;
     const int self = P.self;
     const int nn = P.n_nets;
-    int* sq = det_smem + w * kDetSmemInts;
+    unsigned* slot = det_smem + w * kDetSlots;
+    int* sq = reinterpret_cast<int*>(det_smem + wpb * kDetSlots) + w * kDetSmemInts;
     int* sb = sq + 32;
     int* sp = sb + 32;
     const bool traced = P.trace_cap > 0;
-    unsigned long long seen = 0ull, seen_m = 0ull;
-    for (long long b0 = ((long long)blockIdx.x * wpb + w) * 32; b0 < nn;
-         b0 += (long long)gridDim.x * wpb * 32) {
+    // per lane: nets visited and their members (fewer than 2^31 members in all)
+    unsigned seen = 0u, seen_m = 0u;
+    const DetView& D = P;
+    // Tiles of 32 nets; each warp takes a contiguous run of tiles, so while
+    // it works on one tile the next tile's member ids (which follow this
+    // tile's in m_idx) can be prefetched into L2.
+    const unsigned tiles = ((unsigned)nn + 31u) >> 5;
+    const unsigned nwarps = gridDim.x * wpb;
+    const unsigned per = (tiles + nwarps - 1u) / nwarps;
+    const unsigned t0 = (blockIdx.x * wpb + w) * per;
+    const unsigned t1 = min(tiles, t0 + per);
+    const int m_end = __ldg(P.m_ptr + nn);
+    for (unsigned t = t0; t < t1; ++t) {
+        const unsigned b0 = t << 5;
         const int q = (int)b0 + lane;
         int beg = 0, m = 0;
         if (q < nn && (all || P.net_flag[q] == r)) {
             beg = __ldg(P.m_ptr + q);
             m = __ldg(P.m_ptr + q + 1) - beg + self;
         }
-        if (traced && q < nn && (all || P.net_flag[q] == r)) {
-            seen += 1ull;
-            seen_m += (unsigned long long)m;
+        if (all && t + 1u < t1) {
+            // the next tile's ids: as many 128-byte lines as this tile spans
+            const int e0 = __ldg(P.m_ptr + b0);
+            const int e1 = __ldg(P.m_ptr + b0 + 32u);   // b0 + 32 < nn: a next tile exists
+            const int at = e1 + lane * 32;
+            if (lane * 32 < e1 - e0 && at < m_end) prefetch_l2(P.m_idx + at);
+            if (lane == 0 && b0 + 64u < (unsigned)nn) prefetch_l2(P.m_ptr + b0 + 64u);
+        }
+        if (traced && q < nn && (all || P.net_flag[q] == r)) {   // profiling only
+            seen += 1u;
+            seen_m += (unsigned)m;
         }
         const bool small = m >= 2 && m <= 32;
         const unsigned sm = __ballot_sync(kFullMask, small);
         const unsigned big = __ballot_sync(kFullMask, m > 32);
-        if (sm && __reduce_min_sync(kFullMask, small ? m : 64) > 16) {
+        const int min_small = __reduce_min_sync(kFullMask, small ? m : 64);
+        if (sm == kFullMask && min_small > 16) {
+            // every net of the tile active with 17..32 members: net i is row
+            // i, and its start and size come from lane i
+#pragma unroll 1
+            for (int i0 = 0; i0 < 32; i0 += kDetRows) {
+                int x[kDetRows], id[kDetRows];
+#pragma unroll
+                for (int k = 0; k < kDetRows; ++k) {
+                    const int bg = __shfl_sync(kFullMask, beg, i0 + k);
+                    const int mm = __shfl_sync(kFullMask, m, i0 + k);
+                    id[k] = 1;
+                    x[k] = lane >= mm ? -1
+                           : lane < self ? (int)b0 + i0 + k
+                                         : __ldg(D.m_idx + bg + lane - self);
+                }
+                resolve_rows_iter(D, x, id, r);
+            }
+        } else if (sm && min_small > 16) {
             // every row holds exactly one net
             unsigned rest = sm;
             while (rest) {
@@ -426,11 +572,11 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
                     const int mm = __shfl_sync(kFullMask, m, src);
                     if (lane < mm) {
                         id[k] = 1;
-                        x[k] = self ? (lane == 0 ? qq : __ldg(P.m_idx + bg + lane - 1))
-                                    : __ldg(P.m_idx + bg + lane);
+                        x[k] = self ? (lane == 0 ? qq : __ldg(D.m_idx + bg + lane - 1))
+                                    : __ldg(D.m_idx + bg + lane);
                     }
                 }
-                resolve_rows(P, x, id, seed, r);
+                resolve_rows_iter(D, x, id, r);
             }
         } else if (sm) {
             // exclusive scan of the small nets' sizes = their packed starts
@@ -473,12 +619,15 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
                         const int off = base + lane - sp[i];
                         const int qq = sq[i], bg = sb[i];
                         id[k] = i - r0 + 1;
-                        x[k] = self ? (off == 0 ? qq : __ldg(P.m_idx + bg + off - 1))
-                                    : __ldg(P.m_idx + bg + off);
+                        x[k] = self ? (off == 0 ? qq : __ldg(D.m_idx + bg + off - 1))
+                                    : __ldg(D.m_idx + bg + off);
                     }
                     r0 = r1;
                 }
-                resolve_rows(P, x, id, seed, r);
+                if (PGC_PACKED_SLOTS)
+                    resolve_rows_slots(D, x, id, r, slot);
+                else
+                    resolve_rows_iter(D, x, id, r);
             }
         }
         // nets of more than 32 members, one at a time
@@ -493,11 +642,11 @@ __global__ void net_detect(const Problem* __restrict__ Pp) {
         __syncwarp();
     }
     if (traced) {
-        seen = warp_sum(seen);
-        seen_m = warp_sum(seen_m);
-        if (lane == 0 && seen) {
-            atomicAdd(&P.st->nets_seen, seen);
-            atomicAdd(&P.st->members_seen, seen_m);
+        const unsigned long long a = warp_sum((unsigned long long)seen);
+        const unsigned long long b = warp_sum((unsigned long long)seen_m);
+        if (lane_id() == 0 && a) {
+            atomicAdd(&P.st->nets_seen, a);
+            atomicAdd(&P.st->members_seen, b);
         }
     }
 }
@@ -732,12 +881,16 @@ struct Geometry {
 static pgc_status geometry(const Context& cx, const Opts& o, Geometry* g) {
     g->block = o.block;
     g->smem = (size_t)(o.block / 32) * 2 * kAppendSlots * sizeof(int);
-    g->det_smem = (size_t)(o.block / 32) * kDetSmemInts * sizeof(int);
+    g->det_smem = (size_t)(o.block / 32) * kDetWarpBytes;
     if (g->smem > 48 * 1024) {   // 1024-thread blocks: 64 KB of append buffers
         for (const void* f : {(const void*)net_init, (const void*)net_commit})
             PGC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)g->smem));
     }
+    if (g->det_smem > 48 * 1024)
+        PGC_CUDA(cudaFuncSetAttribute((const void*)net_detect,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)g->det_smem));
     int per_sm = o.grid_per_sm;
     if (per_sm == 0) {
         int a = 0, b = 0;

@@ -106,6 +106,42 @@ def test_pd2_wide_rows(pgc):
     pd2_parity(pgc, b, seed=9)
 
 
+def _splitmix64(x):
+    """splitmix64 (Steele, Lea, Flood 2014) on a uint64 array."""
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def test_pd2_equal_32bit_keys(pgc):
+    """A hub column in all 2^17 rows makes the largest degree 18 bits wide.
+    Detection first compares a 32-bit key (the degree, then the top hash bits
+    that fit), so here only 14 hash bits remain and columns of equal degree in
+    one row often share it; the full key must then decide, as in the oracle."""
+    R, k = 1 << 17, 7
+    half = R * k // 2
+    slots = np.arange(R * k, dtype=np.int64).reshape(R, k)
+    other = 1 + slots % half                      # every other column in exactly 2 rows
+    rows = np.concatenate([np.zeros((R, 1), np.int64), other], axis=1)
+    n_cols = 1 + half
+    row_ptr = np.arange(0, R * (k + 1) + 1, k + 1, dtype=np.int32)
+    col_idx = rows.reshape(-1).astype(np.int32)
+    entry_row = np.repeat(np.arange(R, dtype=np.int32), k + 1)
+    order = np.argsort(col_idx, kind="stable")
+    col_ptr = np.zeros(n_cols + 1, np.int32)
+    col_ptr[1:] = np.cumsum(np.bincount(col_idx, minlength=n_cols))
+    b = gen.Bipartite(R, n_cols, row_ptr, col_idx, col_ptr, entry_row[order])
+    seed = 3
+    # the instance holds many rows with two columns sharing that 32-bit key
+    hi = _splitmix64(np.uint64(seed) ^ other.astype(np.uint64)) >> np.uint64(32)
+    top = (~hi & np.uint64(0xFFFFFFFF)) >> np.uint64(18)
+    top.sort(axis=1)
+    assert np.count_nonzero((top[:, 1:] == top[:, :-1]).any(axis=1)) > 50
+    pd2_parity(pgc, b, seed=seed)
+
+
 def test_d2_equals_pd2_on_closed_neighborhoods(pgc):
     g = gen.random_small(60, 0.08, seed=17)
     b = _graphs.closed_neighborhood_matrix(g)
