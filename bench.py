@@ -632,7 +632,8 @@ def bench_batch(pgc, inputs, torch, dev, num_graphs, peak=None, peak_kind="measu
         nb = d1_algorithmic_bytes(prof.trace_w, prof.trace_s, prof.trace_h, N, E, tail_at, deg)
         top = max(prof.kernel_ms, key=prof.kernel_ms.get)
         out["roofline"] = roofline_entry(top, prof.kernel_ms[top], prof.kernel_launches[top],
-                                         nb[top], peak, peak_kind, "d1_engine.cuh")
+                                         nb[top], peak, peak_kind, "d1_engine.cuh",
+                                         capture=f"{top} (batch)")
         out["kernels"] = kernel_table(prof, nb)
         step_bytes = float(sum(nb.values()))
         out["roofline"]["step_bytes"] = step_bytes
@@ -852,15 +853,17 @@ def dram_ratio(kernel, source):
     return d["dram_bytes"] / d["design_bytes"], d.get("workload")
 
 
-def roofline_entry(kernel, ms_total, launches, bytes_total, peak, peak_kind, source):
+def roofline_entry(kernel, ms_total, launches, bytes_total, peak, peak_kind, source,
+                   capture=None):
     """Roofline of one kernel: design bytes per launch over its average
     CUDA-event launch time, against the measured HBM copy peak; traffic and
     dram_frac from the committed small-case ncu capture scaled by the design
-    bytes (units processed), when the source is unchanged."""
+    bytes (units processed), when the source is unchanged.  capture: the
+    capture's key in the file (default: the kernel name)."""
     avg_s = ms_total / 1000.0 / max(1, launches)
     per = bytes_total / max(1, launches)
     achieved = per / avg_s / 1e9 if avg_s > 0 else None
-    ratio, cap = dram_ratio(kernel, source)
+    ratio, cap = dram_ratio(capture or kernel, source)
     traffic = ratio * per if ratio is not None else None
     out = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak if achieved else None, "traffic": traffic,
@@ -906,7 +909,7 @@ def bench_net(pgc, inputs, torch, dev, reps=5, warm=2, flags=0, timeout_ms=0, pe
                                    prof.trace_members, n, n_nets, members_total)
         top = max(prof.kernel_ms, key=prof.kernel_ms.get)
         rf = roofline_entry(top, prof.kernel_ms[top], prof.kernel_launches[top], nb[top], peak,
-                            peak_kind, "net.cu")
+                            peak_kind, "net.cu", capture=f"{top} ({name})")
         if top == "net_detect":
             rf["method_bytes_per_launch"] = nb["method_detect"] / prof.kernel_launches[top]
         step_bytes = sum(v for k, v in nb.items() if k.startswith("net_"))
@@ -1172,7 +1175,8 @@ def main():
         stop = max(sprof.kernel_ms, key=sprof.kernel_ms.get)
         small["roofline"] = roofline_entry(stop, sprof.kernel_ms[stop],
                                            sprof.kernel_launches[stop], sb[stop], peak,
-                                           peak_kind, "d1_engine.cuh")
+                                           peak_kind, "d1_engine.cuh",
+                                           capture=f"{stop} (small)")
         small["kernels"] = kernel_table(sprof, sb)
         log("[small]", json.dumps({k: v for k, v in small.items() if k != "kernels"}))
     if rank == 0 and not args.no_net:
