@@ -79,6 +79,33 @@ def test_roofline_entry_arithmetic(tmp_path, monkeypatch):
     assert r["traffic"] is None and r["dram_frac"] is None
 
 
+def test_dram_capture_scaling_and_staleness(tmp_path, monkeypatch):
+    """traffic and dram_frac come from a committed small capture, looked up by
+    workload key, scaled by the design bytes, and dropped once the kernel's
+    source file no longer matches the capture's hash."""
+    src = tmp_path / "paper_2107_00075_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "net.cu").write_text("kernel v1")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.source_sha("net.cu")
+    cap = {"net_detect (d2)": {"workload": "w", "dram_bytes": 3e9, "design_bytes": 6e9,
+                               "kernel_source_sha256": sha}}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(cap))
+    r = bench.roofline_entry("net_detect", 2.0, 4, 8e9, 1000.0, "measured", "net.cu",
+                             capture="net_detect (d2)")
+    # 2e9 design bytes per launch, half of them from DRAM, in 0.5 ms
+    assert r["traffic"] == pytest.approx(1e9) and r["dram_frac"] == pytest.approx(2.0)
+    assert r["dram_capture"] == "w"
+    other = bench.roofline_entry("net_detect", 2.0, 4, 8e9, 1000.0, "measured", "net.cu",
+                                 capture="net_detect (pd2)")
+    assert other["traffic"] is None
+    (src / "net.cu").write_text("kernel v2")
+    stale = bench.roofline_entry("net_detect", 2.0, 4, 8e9, 1000.0, "measured", "net.cu",
+                                 capture="net_detect (d2)")
+    assert stale["traffic"] is None and stale["dram_frac"] is None
+
+
 def test_method_bytes_on_a_hand_trace():
     w, s = [10, 6, 2], [40, 30, 8]
     tot, rounds = bench.d1_method_bytes(w, s, 10, 40)
