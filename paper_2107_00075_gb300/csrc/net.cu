@@ -214,15 +214,15 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
         const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
         int t = 0;
         for (int w = 0; w < P.windows && t == 0; ++w) {
-            // four nets at a time: their ids, then their mask words
+            // eight nets at a time: their ids, then their mask words
             const unsigned long long* mw = mk + w * nn;
             unsigned long long f = 0ull;
-            for (int j = 0; j < k; j += 4) {
-                int q[4];
+            for (int j = 0; j < k; j += 8) {
+                int q[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) q[u] = j + u < k ? vertex_net(P, v, beg, j + u) : -1;
+                for (int u = 0; u < 8; ++u) q[u] = j + u < k ? vertex_net(P, v, beg, j + u) : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 8; ++u)
                     if (q[u] >= 0) f |= mw[q[u]];
             }
             if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
@@ -725,8 +725,8 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
     for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < total;
          wbase += stride) {
         const long long i = wbase + lane;
-        bool lost = false, thread_tier = false;
-        int v = -1;
+        bool lost = false, thread_tier = false, won = false;
+        int v = -1, beg = 0, k = 0, t = 0;
         if (i < total) {
             thread_tier = i < nT;
             v = thread_tier ? P.wt[cp][i] : P.ww[cp][i - nT];
@@ -738,17 +738,28 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
                     my_h += (unsigned long long)(d + P.self);
                 }
             } else {
-                const int beg = __ldg(P.r_ptr + v);
-                const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
-                const int t = -P.ck[v].x;
+                won = true;
+                beg = __ldg(P.r_ptr + v);
+                k = __ldg(P.r_ptr + v + 1) - beg + P.self;
+                t = -P.ck[v].x;
                 P.col[v] = t;
                 reinterpret_cast<int*>(P.ck + v)[0] = t;
                 my_max = max(my_max, t);
-                const int w = (t - 1) >> 6;
-                const unsigned long long bit = 1ull << ((t - 1) & 63);
-                for (int j = 0; j < k; ++j)
-                    atomicOr(P.mask + w * nn + vertex_net(P, v, beg, j), bit);
             }
+        }
+        // each winner sets bit t in the masks of its nets, the warp's lanes
+        // taking its nets together (one winner at a time)
+        unsigned wins = __ballot_sync(kFullMask, won);
+        while (wins) {
+            const int src = __ffs(wins) - 1;
+            wins &= wins - 1;
+            const int wv = __shfl_sync(kFullMask, v, src);
+            const int wb = __shfl_sync(kFullMask, beg, src);
+            const int wk = __shfl_sync(kFullMask, k, src);
+            const int wt = __shfl_sync(kFullMask, t, src);
+            unsigned long long* mw = P.mask + (long long)((wt - 1) >> 6) * nn;
+            const unsigned long long bit = 1ull << ((wt - 1) & 63);
+            for (int j = lane; j < wk; j += 32) atomicOr(mw + vertex_net(P, wv, wb, j), bit);
         }
         wa_push(at, lost && thread_tier, v, P.wt[np], &st->nt[np]);
         wa_push(aw, lost && !thread_tier, v, P.ww[np], &st->nw[np]);
