@@ -268,18 +268,20 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
 // Within one net, the members holding tentative color c form a group; every
 // member of the group except its highest-priority one is recolored (Alg. 4
 // applied to each pair of the group).  So a group needs no pairwise loop: its
-// winner is the member with the largest key.  Small nets (2..32 members) are
-// packed whole into "rows" of 32 lanes -- several nets per row -- and four
-// rows are loaded at once so a warp keeps many independent gathers in
-// flight.  Within a row, match.any finds each lane's group; the group's
+// winner is the member with the largest key.  Nets of 17..32 members take one
+// 32-lane row each; smaller ones are packed whole into rows, several nets per
+// row.  A warp loads four one-net rows or two packed rows at once, so it keeps
+// many independent gathers in flight.  Within a row, match.any finds each
+// lane's group.  In one-net rows, two warp-wide max reductions per contested
+// group find its winner; in packed rows, which hold many groups, the group's
 // lowest lane names a shared-memory slot that every member raises to its
-// 32-bit key with one atomic max, so a row costs the same few instructions
-// however many groups it holds.  Larger nets compare every member against
+// 32-bit key with one atomic max.  Larger nets compare every member against
 // every other member, 32 x 32 at a time.
 // ---------------------------------------------------------------------------
-constexpr int kDetRows = 4;        // rows loaded together
+constexpr int kDenseRows = 4;      // rows loaded together: one net per row
+constexpr int kPackedRows = 2;     // rows loaded together: packed small nets
 constexpr int kDetSmemInts = 97;   // per warp: 32 net ids, 32 m_ptr, 33 packed starts
-constexpr int kDetSlots = kDetRows * 32;   // per warp: one max slot per lane of each row
+constexpr int kDetSlots = kPackedRows * 32;   // per warp: one max slot per lane of each packed row
 constexpr size_t kDetWarpBytes = kDetSlots * sizeof(unsigned) + kDetSmemInts * sizeof(int);
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -378,17 +380,19 @@ using DetView = Problem;
 
 // The rows' tentative colors and keys.  t: the group tag (color, net in the
 // row), 0 for a lane that holds no tentative member; g: the lanes sharing it.
+template <int R>
 struct RowState {
-    unsigned t[kDetRows], g[kDetRows], k32[kDetRows];
+    unsigned t[R], g[R], k32[R];
 };
 
-__device__ __forceinline__ void load_rows(const DetView& D, const int (&x)[kDetRows],
-                                          const int (&id)[kDetRows], RowState& S) {
-    int2 p[kDetRows];
+template <int R>
+__device__ __forceinline__ void load_rows(const DetView& D, const int (&x)[R],
+                                          const int (&id)[R], RowState<R>& S) {
+    int2 p[R];
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) p[k] = x[k] >= 0 ? D.ck[x[k]] : make_int2(0, 0);
+    for (int k = 0; k < R; ++k) p[k] = x[k] >= 0 ? D.ck[x[k]] : make_int2(0, 0);
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) {
+    for (int k = 0; k < R; ++k) {
         const int c = p[k].x < 0 ? -p[k].x : 0;
         S.t[k] = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
         S.g[k] = __match_any_sync(kFullMask, S.t[k]);
@@ -400,11 +404,12 @@ __device__ __forceinline__ void load_rows(const DetView& D, const int (&x)[kDetR
 // key (each row's winners outnumber its contested groups): those groups are
 // decided again from the full keys.  Rare: the 32-bit key holds the degree
 // and the top hash bits.
-__device__ __forceinline__ void settle_ties(const DetView& D, const int (&x)[kDetRows],
-                                            const RowState& S, unsigned need,
-                                            bool (&lose)[kDetRows]) {
+template <int R>
+__device__ __forceinline__ void settle_ties(const DetView& D, const int (&x)[R],
+                                            const RowState<R>& S, unsigned need,
+                                            bool (&lose)[R]) {
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) {
+    for (int k = 0; k < R; ++k) {
         if (!(need >> k & 1u)) continue;   // warp-uniform
         const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
         if (contested) lose[k] = group_exact(S.g[k], S.k32[k], x[k], D.key, D.seed);
@@ -415,14 +420,15 @@ __device__ __forceinline__ void settle_ties(const DetView& D, const int (&x)[kDe
 // remaining tag names the next group, a max over its members' keys its
 // winner.  A row with one contested group (every round-1 net) costs two
 // reductions.
-__device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&x)[kDetRows],
-                                                  const int (&id)[kDetRows], int r) {
-    RowState S;
+template <int R>
+__device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&x)[R],
+                                                  const int (&id)[R], int r) {
+    RowState<R> S;
     load_rows(D, x, id, S);
-    bool lose[kDetRows];
+    bool lose[R];
     unsigned need = 0u;
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) {
+    for (int k = 0; k < R; ++k) {
         const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
         unsigned rem = contested ? S.t[k] : 0u, mx = 0u;
         int groups = 0;
@@ -442,7 +448,7 @@ __device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&
     }
     if (need) settle_ties(D, x, S, need, lose);
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k)
+    for (int k = 0; k < R; ++k)
         if (lose[k]) D.lose[x[k]] = r;
 }
 
@@ -450,24 +456,25 @@ __device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&
 // that every member raises to its key with one atomic max.  The cost does
 // not grow with the number of groups in the row.  slot: this warp's
 // kDetSlots words.
-__device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (&x)[kDetRows],
-                                                   const int (&id)[kDetRows], int r,
+template <int R>
+__device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (&x)[R],
+                                                   const int (&id)[R], int r,
                                                    unsigned* slot) {
     const int lane = lane_id();
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) slot[k * 32 + lane] = 0u;
-    RowState S;
+    for (int k = 0; k < R; ++k) slot[k * 32 + lane] = 0u;
+    RowState<R> S;
     load_rows(D, x, id, S);
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k)
+    for (int k = 0; k < R; ++k)
         if (S.t[k] && (S.g[k] & (S.g[k] - 1u)))
             atomicMax(slot + k * 32 + (__ffs(S.g[k]) - 1), S.k32[k]);
     __syncwarp();
-    bool lose[kDetRows];
+    bool lose[R];
     unsigned need = 0u;
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k) {
+    for (int k = 0; k < R; ++k) {
         const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
         const int leader = __ffs(S.g[k]) - 1;
         const unsigned mx = contested ? slot[k * 32 + leader] : 0u;
@@ -479,7 +486,7 @@ __device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (
     __syncwarp();
     if (need) settle_ties(D, x, S, need, lose);
 #pragma unroll
-    for (int k = 0; k < kDetRows; ++k)
+    for (int k = 0; k < R; ++k)
         if (lose[k]) D.lose[x[k]] = r;
 }
 
@@ -542,10 +549,10 @@ __global__ void __maxnreg__(48) net_detect(const Problem* __restrict__ Pp) {
             // every net of the tile active with 17..32 members: net i is row
             // i, and its start and size come from lane i
 #pragma unroll 1
-            for (int i0 = 0; i0 < 32; i0 += kDetRows) {
-                int x[kDetRows], id[kDetRows];
+            for (int i0 = 0; i0 < 32; i0 += kDenseRows) {
+                int x[kDenseRows], id[kDenseRows];
 #pragma unroll
-                for (int k = 0; k < kDetRows; ++k) {
+                for (int k = 0; k < kDenseRows; ++k) {
                     const int bg = __shfl_sync(kFullMask, beg, i0 + k);
                     const int mm = __shfl_sync(kFullMask, m, i0 + k);
                     id[k] = 1;
@@ -559,9 +566,9 @@ __global__ void __maxnreg__(48) net_detect(const Problem* __restrict__ Pp) {
             // every row holds exactly one net
             unsigned rest = sm;
             while (rest) {
-                int x[kDetRows], id[kDetRows];
+                int x[kDenseRows], id[kDenseRows];
 #pragma unroll
-                for (int k = 0; k < kDetRows; ++k) {
+                for (int k = 0; k < kDenseRows; ++k) {
                     x[k] = -1;
                     id[k] = 0;
                     if (!rest) continue;   // warp-uniform
@@ -601,9 +608,9 @@ __global__ void __maxnreg__(48) net_detect(const Problem* __restrict__ Pp) {
             const int cE = lane < cnt ? sp[lane + 1] : 0x7fffffff;
             int r0 = 0;
             while (r0 < cnt) {
-                int x[kDetRows], id[kDetRows];
+                int x[kPackedRows], id[kPackedRows];
 #pragma unroll
-                for (int k = 0; k < kDetRows; ++k) {
+                for (int k = 0; k < kPackedRows; ++k) {
                     x[k] = -1;
                     id[k] = 0;
                     if (r0 >= cnt) continue;   // warp-uniform
