@@ -188,6 +188,13 @@ __device__ __forceinline__ unsigned key32(const Problem& P, int v, int b) {
     return (unsigned)(__ldg(P.key + v) >> b);
 }
 
+// OR of a 64-bit word over the warp
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long f) {
+    const unsigned lo = __reduce_or_sync(kFullMask, (unsigned)f);
+    const unsigned hi = __reduce_or_sync(kFullMask, (unsigned)(f >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
 __device__ __forceinline__ int key_shift(const State* st) {
     const int d = *(volatile const int*)&st->max_deg;
     return d > 0 ? 32 - __clz(d) : 0;
@@ -206,37 +213,90 @@ __global__ void net_assign(const Problem* __restrict__ Pp, cudaGraphConditionalH
     const unsigned long long* mk = P.mask;
     const long long nn = P.n_nets;
     const int kb = key_shift(st);
-    // thread tier
+    // thread tier (at most 64 nets per vertex), a warp's 32 worklist vertices
+    // at a time.  While none has more than 32 nets, each lane walks its own
+    // vertex's nets, eight at a time.  Otherwise (the lanes would idle while
+    // the longest walk finishes) the warp takes the vertices as rows: lane j
+    // reads nets j and j + 32 of the row's vertex (coalesced ids) and an OR
+    // over the lanes gives the forbidden set, four vertices at a time.
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += stride) {
-        const int v = P.wt[cp][i];
-        const int beg = __ldg(P.r_ptr + v);
-        const int k = __ldg(P.r_ptr + v + 1) - beg + P.self;
+    const int lane = lane_id();
+    for (long long wbase = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < nT;
+         wbase += stride) {
+        const long long i = wbase + lane;
+        int v = -1, beg = 0, k = 0;
+        if (i < nT) {
+            v = P.wt[cp][i];
+            beg = __ldg(P.r_ptr + v);
+            k = __ldg(P.r_ptr + v + 1) - beg + P.self;
+        }
         int t = 0;
-        for (int w = 0; w < P.windows && t == 0; ++w) {
-            // eight nets at a time: their ids, then their mask words
-            const unsigned long long* mw = mk + w * nn;
-            unsigned long long f = 0ull;
-            for (int j = 0; j < k; j += 8) {
-                int q[8];
+        if (__reduce_max_sync(kFullMask, (unsigned)k) <= 32u) {
+            if (i < nT) {
+                for (int w = 0; w < P.windows && t == 0; ++w) {
+                    // eight nets at a time: their ids, then their mask words
+                    const unsigned long long* mw = mk + w * nn;
+                    unsigned long long f = 0ull;
+                    for (int j = 0; j < k; j += 8) {
+                        int q[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) q[u] = j + u < k ? vertex_net(P, v, beg, j + u) : -1;
+                        for (int u = 0; u < 8; ++u)
+                            q[u] = j + u < k ? vertex_net(P, v, beg, j + u) : -1;
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (q[u] >= 0) f |= mw[q[u]];
+                        for (int u = 0; u < 8; ++u)
+                            if (q[u] >= 0) f |= mw[q[u]];
+                    }
+                    if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
+                }
+                if (t == 0) {
+                    atomicExch(&st->status, ST_OVERFLOW);
+                    t = 64 * P.windows;
+                }
+                if (mark)
+                    for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
             }
-            if (f != ~0ull) t = 64 * w + __ffsll((long long)~f);
+        } else {
+            const int rows = (int)min(32LL, (long long)nT - wbase);
+            for (int r0 = 0; r0 < rows; r0 += 4) {
+                int q[4][2];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int vv = __shfl_sync(kFullMask, v, r0 + h);
+                    const int bb = __shfl_sync(kFullMask, beg, r0 + h);
+                    const int kk = __shfl_sync(kFullMask, k, r0 + h);
+                    q[h][0] = lane < kk ? vertex_net(P, vv, bb, lane) : -1;
+                    q[h][1] = lane + 32 < kk ? vertex_net(P, vv, bb, lane + 32) : -1;
+                }
+                unsigned long long f[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    f[h] = (q[h][0] >= 0 ? mk[q[h][0]] : 0ull) | (q[h][1] >= 0 ? mk[q[h][1]] : 0ull);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    unsigned long long F = warp_or64(f[h]);
+                    int th = F != ~0ull ? __ffsll((long long)~F) : 0;
+                    for (int w = 1; w < P.windows && th == 0; ++w) {   // warp-uniform, rare
+                        const unsigned long long* mw = mk + w * nn;
+                        F = warp_or64((q[h][0] >= 0 ? mw[q[h][0]] : 0ull) |
+                                      (q[h][1] >= 0 ? mw[q[h][1]] : 0ull));
+                        if (F != ~0ull) th = 64 * w + __ffsll((long long)~F);
+                    }
+                    if (th == 0) {
+                        if (lane == 0 && r0 + h < rows) atomicExch(&st->status, ST_OVERFLOW);
+                        th = 64 * P.windows;
+                    }
+                    if (lane == r0 + h) t = th;
+                    if (mark) {
+                        if (q[h][0] >= 0) mark_net(P, q[h][0], r);
+                        if (q[h][1] >= 0) mark_net(P, q[h][1], r);
+                    }
+                }
+            }
         }
-        if (t == 0) {
-            atomicExch(&st->status, ST_OVERFLOW);
-            t = 64 * P.windows;
-        }
-        P.ck[v] = make_int2(-t, (int)key32(P, v, kb));
-        if (mark)
-            for (int j = 0; j < k; ++j) mark_net(P, vertex_net(P, v, beg, j), r);
+        if (i < nT) P.ck[v] = make_int2(-t, (int)key32(P, v, kb));
     }
     // warp tier
-    const int lane = lane_id(), wpb = blockDim.x >> 5;
+    const int wpb = blockDim.x >> 5;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nW; i += gridDim.x * wpb) {
         const int v = P.ww[cp][i];
         const int beg = __ldg(P.r_ptr + v);
