@@ -18,7 +18,9 @@
 //   detect  per active net: each uncolored member v whose color is also
 //           held by a member with priority loses (Alg. 5 + Alg. 4); small
 //           nets are packed into 32-lane rows and each (net, color) group
-//           keeps only its highest-priority member (warp reductions).
+//           keeps only its highest-priority member (warp reductions).  A
+//           loser is marked by bit 0 of its packed word, written only if the
+//           word the lane loaded does not show it yet.
 //   commit  v in W: losers form W_{r+1}; a winner commits and sets bit t in
 //           the masks of its nets (so a mask is always the OR of its
 //           committed members' colors, kept incrementally: each vertex
@@ -70,9 +72,9 @@ struct Problem {
     const int* r_ptr;     // vertex -> nets
     const int* r_idx;
     int* col;                   // output colors (written at commit)
-    int2* ck;                   // per vertex {color: 0 / -tentative / committed, 32-bit key}
+    int2* ck;                   // per vertex {color: 0 / -tentative / committed, 32-bit key
+                                // whose bit 0 marks a vertex that lost in some net this round}
     unsigned long long* key;    // priority key (see net_init)
-    int* lose;                  // = the round in which the vertex lost (0: never)
     int* net_flag;              // = round number while the net is active
     unsigned long long* mask;   // [window][net]
     int* wt[2];
@@ -140,7 +142,6 @@ __global__ void net_init(const Problem* __restrict__ Pp) {
             P.key[v] = (P.use_deg ? (unsigned long long)d << 32 : 0ull) | (unsigned long long)~hi;
             P.col[v] = 0;
             my_deg = max(my_deg, d);
-            P.lose[v] = 0;
             k = d + P.self;
             long long b = 0;
             for (int j = 0; j < k; ++j) b += net_size(P, vertex_net(P, v, beg, j)) - 1;
@@ -182,10 +183,12 @@ __device__ __forceinline__ void mark_net(const Problem& P, int q, int r) {
 
 // The 32-bit key stored beside the color: key >> b, where b is the bit
 // width of the largest degree term, so the degree still dominates and the
-// top 32 - b hash bits follow.  It orders like the full key except that two
-// different keys may share it; detection resolves such ties from the full key.
+// top 32 - b hash bits follow, with bit 0 cleared: detection sets it on a
+// vertex that loses in some net, and compares keys without it.  It orders
+// like the full key except that two different keys may share it; detection
+// resolves such ties from the full key.
 __device__ __forceinline__ unsigned key32(const Problem& P, int v, int b) {
-    return (unsigned)(__ldg(P.key + v) >> b);
+    return (unsigned)(__ldg(P.key + v) >> b) & ~1u;
 }
 
 // OR of a 64-bit word over the warp
@@ -390,11 +393,14 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
     const unsigned long long seed = P.seed;
     for (int i0 = 0; i0 < m; i0 += 32) {
         int x = -1, c = 0;
+        unsigned kf = 0u;
         unsigned long long kx = 0ull;
         if (i0 + lane < m) {
             x = net_member(P, q, i0 + lane);
-            const int cx = P.ck[x].x;
+            const int2 px = P.ck[x];
+            const int cx = px.x;
             c = cx < 0 ? -cx : 0;
+            kf = (unsigned)px.y;
             if (c) kx = __ldg(P.key + x);
         }
         bool lose = false;
@@ -418,7 +424,7 @@ __device__ void big_net_detect(const Problem& P, int q, int m, int lane, int r) 
                 if (c && cs == c && ys != x && key_priority(ks, ys, kx, x, seed)) lose = true;
             }
         }
-        if (lose) P.lose[x] = r;
+        if (lose && !(kf & 1u)) reinterpret_cast<int*>(P.ck + x)[1] = (int)(kf | 1u);
     }
 }
 
@@ -456,7 +462,7 @@ __device__ __forceinline__ void load_rows(const DetView& D, const int (&x)[R],
         const int c = p[k].x < 0 ? -p[k].x : 0;
         S.t[k] = c ? ((unsigned)c << 5) | (unsigned)(id[k] - 1) : 0u;
         S.g[k] = __match_any_sync(kFullMask, S.t[k]);
-        S.k32[k] = (unsigned)p[k].y;
+        S.k32[k] = (unsigned)p[k].y;   // bit 0: lost in some net this round
     }
 }
 
@@ -472,7 +478,7 @@ __device__ __forceinline__ void settle_ties(const DetView& D, const int (&x)[R],
     for (int k = 0; k < R; ++k) {
         if (!(need >> k & 1u)) continue;   // warp-uniform
         const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
-        if (contested) lose[k] = group_exact(S.g[k], S.k32[k], x[k], D.key, D.seed);
+        if (contested) lose[k] = group_exact(S.g[k], (S.k32[k] & ~1u), x[k], D.key, D.seed);
     }
 }
 
@@ -495,21 +501,21 @@ __device__ __forceinline__ void resolve_rows_iter(const DetView& D, const int (&
         while (__any_sync(kFullMask, rem != 0u)) {   // warp-uniform
             const unsigned tc = __reduce_max_sync(kFullMask, rem);
             const bool in = rem == tc;
-            const unsigned m = __reduce_max_sync(kFullMask, in ? S.k32[k] : 0u);
+            const unsigned m = __reduce_max_sync(kFullMask, in ? (S.k32[k] & ~1u) : 0u);
             if (in) {
                 mx = m;
                 rem = 0u;
             }
             ++groups;
         }
-        lose[k] = contested && S.k32[k] < mx;
-        const int winners = __popc(__ballot_sync(kFullMask, contested && S.k32[k] == mx));
+        lose[k] = contested && (S.k32[k] & ~1u) < mx;
+        const int winners = __popc(__ballot_sync(kFullMask, contested && (S.k32[k] & ~1u) == mx));
         if (winners > groups) need |= 1u << k;
     }
     if (need) settle_ties(D, x, S, need, lose);
 #pragma unroll
     for (int k = 0; k < R; ++k)
-        if (lose[k]) D.lose[x[k]] = r;
+        if (lose[k] && !(S.k32[k] & 1u)) reinterpret_cast<int*>(D.ck + x[k])[1] = (int)(S.k32[k] | 1u);
 }
 
 // Group winners through shared memory: the group's lowest lane names a slot
@@ -529,7 +535,7 @@ __device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (
 #pragma unroll
     for (int k = 0; k < R; ++k)
         if (S.t[k] && (S.g[k] & (S.g[k] - 1u)))
-            atomicMax(slot + k * 32 + (__ffs(S.g[k]) - 1), S.k32[k]);
+            atomicMax(slot + k * 32 + (__ffs(S.g[k]) - 1), (S.k32[k] & ~1u));
     __syncwarp();
     bool lose[R];
     unsigned need = 0u;
@@ -538,8 +544,8 @@ __device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (
         const bool contested = S.t[k] != 0u && (S.g[k] & (S.g[k] - 1u)) != 0u;
         const int leader = __ffs(S.g[k]) - 1;
         const unsigned mx = contested ? slot[k * 32 + leader] : 0u;
-        lose[k] = contested && S.k32[k] < mx;
-        const int winners = __popc(__ballot_sync(kFullMask, contested && S.k32[k] == mx));
+        lose[k] = contested && (S.k32[k] & ~1u) < mx;
+        const int winners = __popc(__ballot_sync(kFullMask, contested && (S.k32[k] & ~1u) == mx));
         const int groups = __popc(__ballot_sync(kFullMask, contested && leader == lane));
         if (winners > groups) need |= 1u << k;
     }
@@ -547,7 +553,7 @@ __device__ __forceinline__ void resolve_rows_slots(const DetView& D, const int (
     if (need) settle_ties(D, x, S, need, lose);
 #pragma unroll
     for (int k = 0; k < R; ++k)
-        if (lose[k]) D.lose[x[k]] = r;
+        if (lose[k] && !(S.k32[k] & 1u)) reinterpret_cast<int*>(D.ck + x[k])[1] = (int)(S.k32[k] | 1u);
 }
 
 #ifndef PGC_PACKED_SLOTS
@@ -797,7 +803,7 @@ __global__ void net_commit(const Problem* __restrict__ Pp, cudaGraphConditionalH
         if (i < total) {
             thread_tier = i < nT;
             v = thread_tier ? P.wt[cp][i] : P.ww[cp][i - nT];
-            if (P.lose[v] == r) {   // lost this round: only the trace needs its degree
+            if (P.ck[v].y & 1) {   // lost this round: only the trace needs its degree
                 lost = true;
                 if (P.trace_cap > 0) {
                     const int d = __ldg(P.r_ptr + v + 1) - __ldg(P.r_ptr + v);
@@ -892,7 +898,7 @@ __global__ void pd2b_combine(const int* __restrict__ rp, const int* __restrict__
 struct Context {
     std::mutex mu;
     DeviceInfo dev;
-    DevBuf key, ck, lose, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col, both[4];
+    DevBuf key, ck, flag, mask, wt, ww, state, problem, trace, stage[4], stage_col, both[4];
     HostBuf h_problem, h_state, h_misc;
     int trace_cap = 0;
     cudaGraph_t graph = nullptr;
@@ -909,7 +915,7 @@ struct Context {
     }
     void release() {
         destroy_graph();
-        for (DevBuf* b : {&key, &ck, &lose, &flag, &mask, &wt, &ww, &state, &problem, &trace,
+        for (DevBuf* b : {&key, &ck, &flag, &mask, &wt, &ww, &state, &problem, &trace,
                           &stage_col, &stage[0], &stage[1], &stage[2], &stage[3], &both[0],
                           &both[1], &both[2], &both[3]})
             b->release();
@@ -1049,7 +1055,6 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
     const int n = in.n;
     if (pgc_status s = cx.key.ensure((size_t)n * 8)) return s;
     if (pgc_status s = cx.ck.ensure((size_t)n * 8)) return s;
-    if (pgc_status s = cx.lose.ensure((size_t)n * 4)) return s;
     if (pgc_status s = cx.flag.ensure((size_t)std::max(in.n_nets, 1) * 4)) return s;
     if (pgc_status s = cx.wt.ensure((size_t)n * 4 * 2)) return s;
     if (pgc_status s = cx.ww.ensure((size_t)n * 4 * 2)) return s;
@@ -1076,7 +1081,6 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
     hp->col = in.col;
     hp->key = cx.key.as<unsigned long long>();
     hp->ck = cx.ck.as<int2>();
-    hp->lose = cx.lose.as<int>();
     hp->net_flag = cx.flag.as<int>();
     for (int p = 0; p < 2; ++p) {
         hp->wt[p] = cx.wt.as<int>() + (size_t)p * n;
@@ -1190,8 +1194,7 @@ static pgc_status run_scratch(Context& cx, const Input& in, uint64_t seed, const
 // ---------------------------------------------------------------------------
 size_t scratch_bytes(int n, int n_nets, int windows) {
     auto a = [](size_t x) { return (x + 255) / 256 * 256; };
-    return a((size_t)n * 8) + a((size_t)n * 8) + a((size_t)n * 4) +
-           a((size_t)std::max(n_nets, 1) * 4) +
+    return a((size_t)n * 8) + a((size_t)n * 8) + a((size_t)std::max(n_nets, 1) * 4) +
            a((size_t)windows * (size_t)std::max(n_nets, 1) * 8) + a((size_t)n * 8) * 2;
 }
 
@@ -1204,8 +1207,6 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     p += a((size_t)n * 8);
     int2* ck = reinterpret_cast<int2*>(p);
     p += a((size_t)n * 8);
-    int* lose = reinterpret_cast<int*>(p);
-    p += a((size_t)n * 4);
     int* flag = reinterpret_cast<int*>(p);
     p += a((size_t)std::max(in.n_nets, 1) * 4);
     unsigned long long* mask = reinterpret_cast<unsigned long long*>(p);
@@ -1230,7 +1231,6 @@ static pgc_status launch_known(Context& cx, void* scratch, const Input& in, int 
     hp->col = in.col;
     hp->key = key;
     hp->ck = ck;
-    hp->lose = lose;
     hp->net_flag = flag;
     hp->mask = mask;
     for (int q = 0; q < 2; ++q) {

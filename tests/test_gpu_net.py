@@ -118,8 +118,9 @@ def _splitmix64(x):
 def test_pd2_equal_32bit_keys(pgc):
     """A hub column in all 2^17 rows makes the largest degree 18 bits wide.
     Detection first compares a 32-bit key (the degree, then the top hash bits
-    that fit), so here only 14 hash bits remain and columns of equal degree in
-    one row often share it; the full key must then decide, as in the oracle."""
+    that fit, the lowest of them cleared), so here only 13 hash bits count and
+    columns of equal degree in one row often share it; the full key must then
+    decide, as in the oracle."""
     R, k = 1 << 17, 7
     half = R * k // 2
     slots = np.arange(R * k, dtype=np.int64).reshape(R, k)
