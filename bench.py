@@ -299,11 +299,12 @@ def net_algorithmic_bytes(trace_w, trace_h, trace_nets, trace_members, n, n_nets
                and when marking its flag read and write 8
       detect:  per visited net offsets 8 (and its flag 4 when marking); per
                member id 4 and packed color and 32-bit key 8 (+ the full key 8
-               for members tied on the short key, not counted); a lose flag per
-               loser 4
-      commit:  per worklist vertex entry 4, lose flag 4; per winner offsets 8,
-               color read and write 8, and per net of a winner its id 4 and
-               mask update 8; per loser its next-round entry 4"""
+               for members tied on the short key, not counted); a loser's flag
+               (bit 0 of its packed word) 4
+      commit:  per worklist vertex entry 4 and its packed {color, key} word
+               8 (whose bit 0 tells a loser); per winner offsets 8, color
+               writes 8, and per net of a winner its id 4 and mask update 8;
+               per loser its next-round entry 4"""
     w = np.asarray(trace_w, dtype=np.float64)
     k = np.asarray(trace_h, dtype=np.float64)
     a = np.asarray(trace_nets, dtype=np.float64)
@@ -314,7 +315,7 @@ def net_algorithmic_bytes(trace_w, trace_h, trace_nets, trace_members, n, n_nets
     init = 28.0 * n + 12.0 * float(k[0] if len(k) else 0.0) + 4.0 * n_nets
     asg = 16.0 * w + (4.0 + 8.0 * windows) * k + 8.0 * k * marking
     det = 8.0 * a + 4.0 * n_nets * marking + 12.0 * m + 4.0 * wn
-    com = 8.0 * w + 16.0 * (w - wn) + 12.0 * (k - kn) + 4.0 * wn
+    com = 12.0 * w + 16.0 * (w - wn) + 12.0 * (k - kn) + 4.0 * wn
     # the method's bytes for detection as the paper states it (nets with a
     # worklist member, 8 per net + 12 per member + the next worklist), for
     # context; round 1 is one pass over every net

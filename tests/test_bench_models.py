@@ -67,7 +67,7 @@ def test_net_bytes_on_a_hand_trace():
     assert b["net_init"] == 28 * 8 + 12 * 20 + 4 * 5
     assert b["net_assign"] == (16 * 8 + 12 * 20) + (16 * 3 + 12 * 9 + 8 * 9)
     assert b["net_detect"] == (8 * 5 + 12 * 30 + 4 * 3) + (8 * 4 + 4 * 5 + 12 * 10)
-    assert b["net_commit"] == (8 * 8 + 16 * 5 + 12 * 11 + 4 * 3) + (8 * 3 + 16 * 3 + 12 * 9)
+    assert b["net_commit"] == (12 * 8 + 16 * 5 + 12 * 11 + 4 * 3) + (12 * 3 + 16 * 3 + 12 * 9)
     assert b["method_detect"] == (8 * 5 + 12 * 30 + 4 * 3) + (8 * 4 + 12 * 10)
 
 
